@@ -1,0 +1,155 @@
+"""CPU oracle for projective TSDF integration — TEST INFRASTRUCTURE ONLY.
+
+A plain FP64 restatement of nvblox's frame integration (Sec. IV-B, Eq. 1-3)
+in ``tsdf_oracle.cpp``, loaded through ctypes.  Only the test suite, the
+package smoke check and the benchmark's CPU-baseline leg may import this
+module; the product path never does, and it shares no code with the CUDA
+path.  See the header of ``tsdf_oracle.cpp`` for the precision contract
+(FP64 values, prescribed FP32 decisions).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tsdf_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile tsdf_oracle.cpp into liboracle.so (g++, FP contraction off)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+           _SRC, "-o", _LIB + ".tmp"]
+    try:
+        subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(cmd, check=True, capture_output=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P, F, I, L, D = (ctypes.c_void_p, ctypes.c_float, ctypes.c_int32, ctypes.c_int64,
+                             ctypes.c_double)
+            lib.orc_create.argtypes = [F, I, F]
+            lib.orc_create.restype = P
+            lib.orc_destroy.argtypes = [P]
+            lib.orc_set_lidar_sampling.argtypes = [P, I, F]
+            lib.orc_integrate_pinhole.argtypes = [P, P, I, I, F, F, F, F, P]
+            lib.orc_integrate_pinhole.restype = I
+            lib.orc_integrate_lidar.argtypes = [P, P, I, I, F, F, F, F, F, P]
+            lib.orc_integrate_lidar.restype = I
+            lib.orc_num_blocks.argtypes = [P]
+            lib.orc_num_blocks.restype = L
+            lib.orc_export.argtypes = [P, P, P, P, L]
+            lib.orc_export.restype = L
+            lib.orc_last_band.argtypes = [P, P, L]
+            lib.orc_last_band.restype = L
+            lib.orc_counters.argtypes = [P, P]
+            lib.orc_atan2_dec.argtypes = [F, F]
+            lib.orc_atan2_dec.restype = F
+            lib.orc_dda.argtypes = [P, P, F, F, P]
+            lib.orc_dda.restype = I
+            _lib = lib
+            del D
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class OracleMap:
+    """One TSDF layer held by the oracle (map_create analogue)."""
+
+    def __init__(self, voxel_size: float, truncation_voxels: int = 4, max_weight: float = 100.0):
+        self._lib = _load()
+        self._h = self._lib.orc_create(voxel_size, truncation_voxels, max_weight)
+        self.voxel_size = float(np.float32(voxel_size))
+        self.truncation_voxels = truncation_voxels
+        self.max_weight = max_weight
+
+    def close(self):
+        if self._h:
+            self._lib.orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_lidar_sampling(self, nearest: bool = False, guard: float = 0.0):
+        self._lib.orc_set_lidar_sampling(self._h, int(nearest), guard)
+
+    def integrate(self, sensor: dict, T: np.ndarray, depth: np.ndarray):
+        depth = np.ascontiguousarray(depth, np.float32)
+        T = np.ascontiguousarray(T, np.float64).reshape(16)
+        if sensor["kind"] == "pinhole":
+            assert depth.shape == (sensor["height"], sensor["width"])
+            rc = self._lib.orc_integrate_pinhole(self._h, _p(depth), sensor["width"],
+                                                 sensor["height"], sensor["fu"], sensor["fv"],
+                                                 sensor["cu"], sensor["cv"], _p(T))
+        else:
+            assert depth.shape == (sensor["n_el"], sensor["n_az"])
+            rc = self._lib.orc_integrate_lidar(self._h, _p(depth), sensor["n_az"], sensor["n_el"],
+                                               sensor["theta_start"], sensor["phi_start"],
+                                               sensor["el_fov"], sensor["min_range"],
+                                               sensor["max_range"], _p(T))
+        if rc != 0:
+            raise RuntimeError(f"oracle integrate failed ({rc})")
+
+    def num_blocks(self) -> int:
+        return int(self._lib.orc_num_blocks(self._h))
+
+    def export(self, with_values: bool = True):
+        """(keys int32[n,3] sorted by (x,y,z), D float64[n,512], W float64[n,512])."""
+        n = self.num_blocks()
+        keys = np.zeros((n, 3), np.int32)
+        D = np.zeros((n, 512), np.float64) if with_values else None
+        W = np.zeros((n, 512), np.float64) if with_values else None
+        got = self._lib.orc_export(self._h, _p(keys), _p(D) if with_values else None,
+                                   _p(W) if with_values else None, n)
+        assert got == n
+        return keys, D, W
+
+    def last_band(self) -> np.ndarray:
+        n = int(self.counters()["band_blocks"])
+        keys = np.zeros((n, 3), np.int32)
+        got = self._lib.orc_last_band(self._h, _p(keys), n)
+        assert got == n
+        return keys
+
+    def counters(self) -> dict:
+        out = np.zeros(6, np.int64)
+        self._lib.orc_counters(self._h, _p(out))
+        names = ["candidates", "band_blocks", "new_blocks", "voxels_updated", "truncated_rays",
+                 "total_updates"]
+        return dict(zip(names, (int(x) for x in out)))
+
+
+def atan2_dec(y: float, x: float) -> float:
+    return float(_load().orc_atan2_dec(y, x))
+
+
+def dda(o, direction, s0: float, s1: float) -> np.ndarray:
+    """Cells (anchor-relative, int32[n,3]) of the oracle's block traversal."""
+    o = np.ascontiguousarray(o, np.float32)
+    direction = np.ascontiguousarray(direction, np.float32)
+    cells = np.zeros((32, 3), np.int32)
+    n = _load().orc_dda(_p(o), _p(direction), s0, s1, _p(cells))
+    return cells[:n].copy()

@@ -1,0 +1,414 @@
+"""Pins for the CPU oracle: closed forms, counting invariants, brute force.
+
+Each test derives its expected values from the scene geometry and the
+method's definition (nvblox Sec. IV-B, Eq. 1-3) with the independent FP64
+helpers in refgeom.py, never from the oracle itself.  Voxels whose discrete
+decisions (pixel rounding, image border, the d_p >= -tau test, LiDAR cell
+choice) fall within a small margin of a tie are left out, since the oracle
+takes those decisions in prescribed FP32 arithmetic.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import PLANE, SPHERE, prim, scene
+from tests import refgeom as G
+
+F32 = lambda x: float(np.float32(x))  # noqa: E731
+
+
+def _tau(v, trunc=4):
+    return trunc * F32(v)
+
+
+def _run(vox, frames, trunc=4, wmax=100.0):
+    m = oracle.OracleMap(vox, trunc, wmax)
+    for cam, T, d in frames:
+        m.integrate(cam, T, d)
+    return m
+
+
+def _check_pinhole_single(cam, T, depth_expected, keys, D, W, v, tau, px_margin=1e-3,
+                          dp_margin=1e-5, tol=1e-9):
+    """Compare one-frame oracle output with the update rule evaluated in FP64
+    on `depth_expected` (float32-rounded closed-form or brute-force depths)."""
+    pL = G.voxel_centres(keys, v)
+    pC = G.to_sensor(T, pL)
+    i, j, inside, ok = G.pinhole_pixel(cam, pC, px_margin)
+    ic = np.clip(i, 0, cam["width"] - 1)
+    jc = np.clip(j, 0, cam["height"] - 1)
+    d = depth_expected[jc, ic].astype(np.float64)
+    valid = inside & (d > 0) & np.isfinite(d)
+    dp = d - pC[..., 2]
+    upd = valid & (dp >= -tau)
+    ok &= ~valid | (np.abs(dp + tau) > dp_margin)
+    W_exp = upd.astype(np.float64)
+    D_exp = np.where(upd, np.minimum(dp, tau), 0.0)
+    n_ok = int(ok.sum())
+    assert n_ok > 0.9 * ok.size, "too many ambiguous voxels for a meaningful pin"
+    np.testing.assert_array_equal(W[ok], W_exp[ok])
+    np.testing.assert_allclose(D[ok], D_exp[ok], rtol=0, atol=tol)
+    return int(upd[ok].sum())
+
+
+def _check_blocks(keys, definite, possible):
+    got = {tuple(k) for k in keys.tolist()}
+    missing = definite - got
+    extra = got - possible
+    assert not missing, f"{len(missing)} blocks met by a band segment were not allocated"
+    assert not extra, f"{len(extra)} allocated blocks are not met by any band segment"
+
+
+# ---------------------------------------------------------------- pinhole
+
+
+def test_plane_closed_form_identity():
+    """Fronto-parallel plane z = 2 m seen from the identity pose: every pixel
+    has depth 2, so D = min(2 - z_v, tau) and W = 1 wherever d_p >= -tau."""
+    cam = synth.pinhole(64, 48, 50.0, 32.0, 24.0)
+    prims = scene(prim(PLANE, 0, 0, 1, 2.0))
+    T = np.eye(4)
+    depth = synth.render_pinhole(prims, T, cam["fu"], cam["fv"], cam["cu"], cam["cv"], 64, 48)
+    assert np.all(depth == np.float32(2.0))
+    v = F32(0.05)
+    tau = _tau(v)
+    m = _run(0.05, [(cam, T, depth)])
+    keys, D, W = m.export()
+    # closed-form block set: blocks met by the segments z in [1.8, 2.2]
+    definite, possible = G.pinhole_band_blocks(cam, T, np.full((48, 64), 2.0), tau, 8 * v)
+    _check_blocks(keys, definite, possible)
+    n = _check_pinhole_single(cam, T, np.full((48, 64), np.float32(2.0)), keys, D, W, v, tau)
+    assert n == m.counters()["voxels_updated"]
+    # every updated voxel in front of the band edge carries exactly +tau
+    z = G.voxel_centres(keys, v)[..., 2]
+    sel = (W == 1) & (z < 2.0 - tau - 1e-6)
+    assert sel.sum() > 0 and np.all(D[sel] == tau)
+    # occluded voxels (more than tau behind the surface) are never updated
+    assert np.all(W[z > 2.0 + tau + 1e-6] == 0)
+
+
+def _sphere_depth(cam, c, R, plane_z):
+    """Closed-form z-depth per pixel: nearer of the sphere and plane hits."""
+    H, W = cam["height"], cam["width"]
+    jj, ii = np.mgrid[0:H, 0:W]
+    r = np.stack([(ii - cam["cu"]) / cam["fu"], (jj - cam["cv"]) / cam["fv"], np.ones_like(ii, float)], -1)
+    rr = (r * r).sum(-1)
+    rc = (r * c).sum(-1)
+    disc = rc * rc - rr * (c @ c - R * R)
+    with np.errstate(invalid="ignore"):
+        t = (rc - np.sqrt(disc)) / rr
+    t = np.where(disc >= 0, t, np.inf)
+    return np.minimum(t, plane_z).astype(np.float32)
+
+
+def test_sphere_closed_form_tiny():
+    """The tiny workload: plane z = 2 plus a sphere r = 0.3 at (0.2, 0.1, 1.5);
+    the pixel depth is the smaller root of |t r - c|^2 = R^2 (r_z = 1)."""
+    w = synth.config_tiny()
+    f = w.frames[0]
+    exp_depth = _sphere_depth(f.sensor, np.array([0.2, 0.1, 1.5]), 0.3, 2.0)
+    np.testing.assert_allclose(f.depth, exp_depth, rtol=2e-7, atol=0)
+    v = F32(w.voxel_size)
+    tau = _tau(v)
+    m = _run(w.voxel_size, [(f.sensor, f.T, f.depth)])
+    keys, D, W = m.export()
+    definite, possible = G.pinhole_band_blocks(f.sensor, f.T, exp_depth, tau, 8 * v)
+    _check_blocks(keys, definite, possible)
+    _check_pinhole_single(f.sensor, f.T, exp_depth, keys, D, W, v, tau)
+    # the sphere produces distinct per-pixel depths, so pixel choice matters
+    assert len(np.unique(exp_depth)) > 100
+
+
+def _random_rotation(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    a, b, c, d = q
+    return np.array([[a*a+b*b-c*c-d*d, 2*(b*c-a*d), 2*(b*d+a*c)],
+                     [2*(b*c+a*d), a*a-b*b+c*c-d*d, 2*(c*d-a*b)],
+                     [2*(b*d-a*c), 2*(c*d+a*b), a*a-b*b-c*c+d*d]])
+
+
+@pytest.mark.parametrize("seed,origin", [(1, (103.7, -52.1, 7.3)), (2, (-0.3, 0.2, -0.9)),
+                                         (3, (-2001.13, 17.9, -3.31))])
+def test_tilted_plane_general_pose(seed, origin):
+    """Tilted plane seen from a general pose far from the origin (negative
+    block coordinates, anchor-local arithmetic): closed-form depth
+    t = (c - n.o) / (n . R r) per pixel."""
+    rng = np.random.default_rng(seed)
+    R = _random_rotation(rng)
+    T = np.eye(4)
+    T[:3, :3] = R
+    T[:3, 3] = origin
+    fwd = R[:, 2]
+    n = fwd + 0.4 * rng.normal(size=3)
+    n /= np.linalg.norm(n)
+    c = float(n @ (T[:3, 3] + 1.7 * fwd))
+    cam = synth.pinhole(40, 30, 30.0)
+    prims = scene(prim(PLANE, *n, c))
+    depth = synth.render_pinhole(prims, T, cam["fu"], cam["fv"], cam["cu"], cam["cv"], 40, 30,
+                                 max_depth=6.0)
+    jj, ii = np.mgrid[0:30, 0:40]
+    r = np.stack([(ii - cam["cu"]) / cam["fu"], (jj - cam["cv"]) / cam["fv"], np.ones((30, 40))], -1)
+    t_exp = (c - n @ T[:3, 3]) / ((r @ R.T) @ n)
+    t_exp = np.where((t_exp > 0) & (t_exp <= 6.0), t_exp, 0.0).astype(np.float32)
+    np.testing.assert_allclose(depth, t_exp, rtol=1e-6, atol=0)
+    v = F32(0.05)
+    tau = _tau(v)
+    m = _run(0.05, [(cam, T, depth)])
+    keys, D, W = m.export()
+    definite, possible = G.pinhole_band_blocks(cam, T, t_exp, tau, 8 * v)
+    _check_blocks(keys, definite, possible)
+    _check_pinhole_single(cam, T, t_exp, keys, D, W, v, tau)
+
+
+def test_brute_force_room_frame():
+    """A small frame of the seeded room from a pose on its trajectory: the
+    block set against a slab test over every pixel's band segment, and every
+    voxel of every block against the update rule evaluated in FP64."""
+    prims = synth.room_scene(7)
+    Ts = synth.trajectory(7, prims, 5)
+    cam = synth.pinhole(48, 36, 40.0)
+    for T in Ts[::2]:
+        depth = synth.render_frame(prims, cam, T, {"sigma_z2": 0.0012, "invalid_frac": 0.05,
+                                                   "max_depth": 5.0}, 7, 0)
+        v = F32(0.05)
+        tau = _tau(v)
+        m = _run(0.05, [(cam, T, depth)])
+        keys, D, W = m.export()
+        definite, possible = G.pinhole_band_blocks(cam, T, depth, tau, 8 * v)
+        _check_blocks(keys, definite, possible)
+        _check_pinhole_single(cam, T, depth, keys, D, W, v, tau)
+
+
+def test_weight_counts_repeated_frame():
+    """Integrating the same frame K = 150 times: W = min(K, 100) on every
+    voxel the single frame updated, 0 elsewhere, and D unchanged."""
+    w = synth.config_tiny()
+    f = w.frames[0]
+    m1 = _run(w.voxel_size, [(f.sensor, f.T, f.depth)])
+    k1, D1, W1 = m1.export()
+    mk = _run(w.voxel_size, [(f.sensor, f.T, f.depth)] * 150)
+    kk, Dk, Wk = mk.export()
+    np.testing.assert_array_equal(k1, kk)
+    np.testing.assert_array_equal(Wk, np.where(W1 > 0, 100.0, 0.0))
+    np.testing.assert_allclose(Dk, D1, rtol=0, atol=1e-12)
+    assert mk.counters()["total_updates"] == 150 * m1.counters()["voxels_updated"]
+
+
+def test_weighted_average_and_cap_closed_form():
+    """60 frames at depth d1 then 40 at d2: D is the arithmetic mean of the
+    truncated distances (W = 100); then 37 frames at d3: past the cap the
+    average is an exponential one, D = s3 + (100/101)^37 (mean - s3)."""
+    cam = synth.pinhole(32, 24, 25.0)
+    T = np.eye(4)
+    ds = [2.0, 2.03, 1.97]
+    imgs = [synth.render_pinhole(scene(prim(PLANE, 0, 0, 1, d)), T, cam["fu"], cam["fv"],
+                                 cam["cu"], cam["cv"], 32, 24) for d in ds]
+    frames = [(cam, T, imgs[0])] * 60 + [(cam, T, imgs[1])] * 40
+    m = _run(0.05, frames)
+    keys, D, W = m.export()
+    v = F32(0.05)
+    tau = _tau(v)
+    z = G.voxel_centres(keys, v)[..., 2]
+    s = [np.minimum(float(np.float32(d)) - z, tau) for d in ds]
+    pC = G.to_sensor(T, G.voxel_centres(keys, v))
+    _, _, inside, ok = G.pinhole_pixel(cam, pC, 1e-3)
+    sel = inside & ok & (z < 1.97 - tau - 0.01) | (inside & ok & (z > 1.5) & (z < 2.1))
+    sel &= (float(np.float32(1.97)) - z >= -tau + 1e-5)
+    assert sel.sum() > 100
+    np.testing.assert_array_equal(W[sel], 100.0)
+    np.testing.assert_allclose(D[sel], (60 * s[0][sel] + 40 * s[1][sel]) / 100, rtol=0, atol=1e-12)
+    mean = D.copy()
+    for _ in range(37):
+        m.integrate(cam, T, imgs[2])
+    keys2, D2, W2 = m.export()
+    np.testing.assert_array_equal(keys, keys2)
+    expect = s[2] + (100.0 / 101.0) ** 37 * (mean - s[2])
+    np.testing.assert_array_equal(W2[sel], 100.0)
+    np.testing.assert_allclose(D2[sel], expect[sel], rtol=0, atol=1e-12)
+
+
+def test_dda_matches_slab_test():
+    """The oracle's block traversal against a slab test on random segments."""
+    rng = np.random.default_rng(11)
+    B = 1.0
+    n_checked = 0
+    for _ in range(3000):
+        o = rng.uniform(0, 1, 3).astype(np.float32)
+        d = rng.normal(size=3).astype(np.float32) * rng.uniform(0.1, 3)
+        if rng.uniform() < 0.2:
+            d[rng.integers(3)] = 0.0  # axis-parallel segments
+        s0 = np.float32(rng.uniform(0, 4))
+        s1 = np.float32(s0 + rng.uniform(0, 2))
+        cells = oracle.dda(o, d, float(s0), float(s1))
+        got = {tuple(c) for c in cells.tolist()}
+        definite, possible = G.segment_cells(o.astype(np.float64), d.astype(np.float64),
+                                             float(s0), float(s1), B, 1e-4, 1e-5)
+        assert definite <= got <= possible, (o, d, s0, s1)
+        # cells are emitted as a face-connected walk
+        steps = np.abs(np.diff(cells, axis=0)).sum(1)
+        assert np.all(steps == 1)
+        n_checked += 1
+    assert n_checked == 3000
+
+
+# ------------------------------------------------------------------ LiDAR
+
+
+def test_atan2_dec_error_bound():
+    """The FP32 atan2 used for decisions stays within 4 ulp of atan2 and
+    keeps the quadrant conventions of atan2."""
+    rng = np.random.default_rng(5)
+    ys = np.concatenate([rng.normal(size=20000) * 10 ** rng.uniform(-3, 3, 20000),
+                         [0.0, 1.0, -1.0, 1.0, -1.0, 0.0, 3.0]]).astype(np.float32)
+    xs = np.concatenate([rng.normal(size=20000) * 10 ** rng.uniform(-3, 3, 20000),
+                         [1.0, 1.0, 1.0, -1.0, -1.0, -2.0, 0.0]]).astype(np.float32)
+    worst = 0.0
+    for y, x in zip(ys.tolist(), xs.tolist()):
+        a = oracle.atan2_dec(y, x)
+        e = math.atan2(y, x)
+        ulp = np.spacing(np.float32(abs(e))) if e != 0 else np.float32(1e-45)
+        err = abs(a - e) / float(ulp)
+        worst = max(worst, err)
+    assert worst <= 4.0, worst
+    assert oracle.atan2_dec(0.0, -2.0) == F32(math.pi)
+    assert oracle.atan2_dec(3.0, 0.0) == F32(math.pi / 2)
+
+
+def _lidar_pose(seed):
+    rng = np.random.default_rng(seed)
+    T = np.eye(4)
+    T[:3, :3] = _random_rotation(rng)
+    T[:3, 3] = rng.uniform(-50, 50, 3)
+    return T
+
+
+def _check_lidar_single(lid, T, rng_img, keys, D, W, v, tau, guard, exp_fn=None, tol=1e-9):
+    pC = G.to_sensor(T, G.voxel_centres(keys, v))
+    u, vv, r = G.lidar_coords(lid, pC)
+    d, valid, ok = G.lidar_bilinear(lid, rng_img, u, vv, guard)
+    dp = d - r
+    upd = valid & (dp >= -tau)
+    ok &= ~valid | (np.abs(dp + tau) > 1e-5)
+    assert ok.mean() > 0.9
+    np.testing.assert_array_equal(W[ok], upd[ok].astype(float))
+    D_exp = np.where(upd, np.minimum(dp, tau), 0.0)
+    np.testing.assert_allclose(D[ok], D_exp[ok], rtol=0, atol=tol)
+    return upd, ok
+
+
+def test_lidar_inside_sphere_closed_form():
+    """A LiDAR at the centre of a sphere of radius 10 m sees a constant range
+    image, so bilinear sampling is exact and D = min(10 - |p|, tau)."""
+    lid = synth.lidar64(n_az=128, n_el=16)
+    T = _lidar_pose(3)
+    img = np.full((16, 128), 10.0, np.float32)
+    v = F32(0.05)
+    tau = _tau(v)
+    m = oracle.OracleMap(0.05)
+    m.integrate(lid, T, img)
+    keys, D, W = m.export()
+    definite, possible = G.lidar_band_blocks(lid, T, img, tau, 8 * v)
+    _check_blocks(keys, definite, possible)
+    upd, ok = _check_lidar_single(lid, T, img, keys, D, W, v, tau, tau)
+    r = np.linalg.norm(G.to_sensor(T, G.voxel_centres(keys, v)), axis=-1)
+    sel = upd & ok
+    np.testing.assert_allclose(D[sel], np.minimum(10.0 - r[sel], tau), rtol=0, atol=1e-9)
+    assert sel.sum() > 1000
+
+
+def test_lidar_bilinear_and_azimuth_wrap():
+    """A smooth range image periodic in azimuth: the oracle's sample equals
+    bilinear interpolation between the four surrounding beam centres,
+    wrapping across the first/last column."""
+    lid = synth.lidar64(n_az=96, n_el=12)
+    T = _lidar_pose(4)
+    k = np.arange(96)
+    j = np.arange(12)
+    th = lid["theta_start"] + (k + 0.5) * 2 * math.pi / 96
+    img = (8.0 + 0.06 * np.cos(th)[None, :] + 0.01 * j[:, None]).astype(np.float32)
+    v = F32(0.05)
+    tau = _tau(v)
+    m = oracle.OracleMap(0.05)
+    m.integrate(lid, T, img)
+    keys, D, W = m.export()
+    upd, ok = _check_lidar_single(lid, T, img, keys, D, W, v, tau, tau, tol=2e-6)
+    pC = G.to_sensor(T, G.voxel_centres(keys, v))
+    u, _, _ = G.lidar_coords(lid, pC)
+    seam = (u - 0.5 < 0) | (u - 0.5 >= 95)
+    assert (upd & ok & seam).sum() > 50, "no voxel sampled across the azimuth seam"
+
+
+def test_lidar_guard_skips_fg_bg_edges():
+    """A range step of 3 m between two halves of the image: voxels whose four
+    neighbouring beams straddle the step are not updated (guard), the others
+    are."""
+    lid = synth.lidar64(n_az=64, n_el=8)
+    T = _lidar_pose(5)
+    img = np.full((8, 64), 6.0, np.float32)
+    img[:, 20:40] = 9.0
+    v = F32(0.05)
+    tau = _tau(v)
+    m = oracle.OracleMap(0.05)
+    m.integrate(lid, T, img)
+    keys, D, W = m.export()
+    upd, ok = _check_lidar_single(lid, T, img, keys, D, W, v, tau, tau, tol=2e-6)
+    pC = G.to_sensor(T, G.voxel_centres(keys, v))
+    u, vv, r = G.lidar_coords(lid, pC)
+    k0 = np.floor(u - 0.5).astype(int) % 64
+    straddle = np.isin(k0, [19, 39]) & ok & (np.floor(vv - 0.5) >= 0) & (np.floor(vv - 0.5) <= 6)
+    assert straddle.sum() > 20
+    assert np.all(W[straddle] == 0)
+
+
+def test_lidar_nearest_mode():
+    """Nearest-cell sampling (test mode): the cell containing (u, v)."""
+    lid = synth.lidar64(n_az=64, n_el=8)
+    T = _lidar_pose(6)
+    rng = np.random.default_rng(0)
+    img = rng.uniform(5.0, 5.1, (8, 64)).astype(np.float32)
+    v = F32(0.05)
+    tau = _tau(v)
+    m = oracle.OracleMap(0.05)
+    m.set_lidar_sampling(nearest=True)
+    m.integrate(lid, T, img)
+    keys, D, W = m.export()
+    pC = G.to_sensor(T, G.voxel_centres(keys, v))
+    u, vv, r = G.lidar_coords(lid, pC)
+    kk, jj = np.floor(u).astype(int), np.floor(vv).astype(int)
+    fu, fv = u - kk, vv - jj
+    ok = (np.minimum(fu, 1 - fu) > 1e-3) & (np.minimum(fv, 1 - fv) > 1e-3)
+    inrow = (jj >= 0) & (jj < 8)
+    d = img[np.clip(jj, 0, 7), kk % 64].astype(float)
+    dp = d - r
+    ok &= np.abs(dp + tau) > 1e-5
+    upd = inrow & (dp >= -tau)
+    np.testing.assert_array_equal(W[ok], upd[ok].astype(float))
+    np.testing.assert_allclose(D[ok], np.where(upd, np.minimum(dp, tau), 0)[ok], atol=1e-9)
+
+
+def test_lidar_brute_force_outdoor():
+    """A LiDAR scan of the seeded outdoor scene: block set against the slab
+    test over every beam's band segment; voxels against the guarded bilinear
+    update rule in FP64."""
+    prims = synth.outdoor_scene(9, n_boxes=60, n_cyl=20, size=(20.0, 20.0, 5.0))
+    lid = synth.lidar64(n_az=180, n_el=16, max_range=30.0)
+    T = np.eye(4)
+    T[:3, 3] = [10.0, 10.0, 1.5]
+    img = synth.render_frame(prims, lid, T, {"sigma": 0.0}, 9, 0)
+    v = F32(0.1)
+    tau = _tau(v)
+    m = oracle.OracleMap(0.1)
+    m.integrate(lid, T, img)
+    keys, D, W = m.export()
+    definite, possible = G.lidar_band_blocks(lid, T, img, tau, 8 * v)
+    _check_blocks(keys, definite, possible)
+    # the oracle takes the sample position (u, v) in FP32 (a decision input):
+    # its error, below 1e-4 px at these image sizes, times the largest spread
+    # the guard lets through (tau) bounds the difference to FP64 bilinear.
+    _check_lidar_single(lid, T, img, keys, D, W, v, tau, tau, tol=1e-4 * tau)
