@@ -331,7 +331,8 @@ def test_lidar_bilinear_and_azimuth_wrap():
     k = np.arange(96)
     j = np.arange(12)
     th = lid["theta_start"] + (k + 0.5) * 2 * math.pi / 96
-    img = (8.0 + 0.06 * np.cos(th)[None, :] + 0.01 * j[:, None]).astype(np.float32)
+    img = (8.0 + 0.06 * np.sin(th)[None, :] + 0.02 * np.cos(th)[None, :]
+           + 0.01 * j[:, None]).astype(np.float32)
     v = F32(0.05)
     tau = _tau(v)
     m = oracle.OracleMap(0.05)
