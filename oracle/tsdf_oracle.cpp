@@ -154,8 +154,16 @@ int dda(const float o[3], const float dir[3], float s0, float s1, int32_t cells[
         int* truncated) {
   int c[3], step[3];
   float inv[3], tmax[3];
+  *truncated = 0;
+  float start[3];
   for (int k = 0; k < 3; ++k) {
-    c[k] = (int)std::floor(std::fmaf(s0, dir[k], o[k]));
+    start[k] = std::fmaf(s0, dir[k], o[k]);
+    // keys hold 21-bit coordinates: a segment that starts 2^18 blocks or
+    // more from the sensor's block is outside the map's range and dropped
+    if (!(std::fabs(start[k]) < 262144.0f)) return 0;
+  }
+  for (int k = 0; k < 3; ++k) {
+    c[k] = (int)std::floor(start[k]);
     step[k] = dir[k] > 0.0f ? 1 : (dir[k] < 0.0f ? -1 : 0);
     inv[k] = step[k] != 0 ? 1.0f / dir[k] : 0.0f;
   }
@@ -168,7 +176,6 @@ int dda(const float o[3], const float dir[3], float s0, float s1, int32_t cells[
   int n = 0;
   for (int k = 0; k < 3; ++k) cells[n][k] = c[k];
   ++n;
-  *truncated = 0;
   while (true) {
     int k = 0;
     if (tmax[1] < tmax[k]) k = 1;
@@ -278,6 +285,9 @@ int32_t orc_integrate_pinhole(void* h, const float* depth, int32_t W, int32_t H,
                               float fv, float cu, float cv, const double* T) {
   Oracle& m = *static_cast<Oracle*>(h);
   const Pose P = make_pose(T, m.Bd);
+  // block coordinates are 21-bit: the sensor's block must lie within 2^19
+  for (int c = 0; c < 3; ++c)
+    if (!(P.a[c] > -524288 && P.a[c] < 524288)) return -1;
   m.last = Counters();
   const float tau = m.tauf;
 
@@ -369,6 +379,9 @@ int32_t orc_integrate_lidar(void* h, const float* range, int32_t n_az, int32_t n
                             float max_range, const double* T) {
   Oracle& m = *static_cast<Oracle*>(h);
   const Pose P = make_pose(T, m.Bd);
+  // block coordinates are 21-bit: the sensor's block must lie within 2^19
+  for (int c = 0; c < 3; ++c)
+    if (!(P.a[c] > -524288 && P.a[c] < 524288)) return -1;
   m.last = Counters();
   const float tau = m.tauf;
   auto valid = [&](float d) { return d >= min_range && d <= max_range; };
