@@ -1,0 +1,197 @@
+/*
+ * tsdf.h — C ABI of the GB300 projective TSDF integration library.
+ *
+ * The library builds the TSDF layer of a sparse voxel map from depth images
+ * (nvblox, Sec. IV "System architecture"): the map is a hash table from
+ * integer 3D block coordinates to 8x8x8-voxel blocks stored contiguously in
+ * GPU memory (Sec. IV-A "The Map"), and every frame is integrated by
+ * allocating the blocks in view and running a per-voxel projective update
+ * (Sec. IV-B "Frame Integration", Eq. 1-3).  Sensors follow the problem
+ * statement (Sec. III): a depth image D: Omega -> d with Omega the pinhole
+ * image plane (z-depth) or the LiDAR beam angles (range), taken at a pose
+ * T_LC in SE(3) of the sensor in the layer frame.
+ *
+ * Conventions shared by every call:
+ *  - All buffers are owned by the caller.  Pointers named *_dev are device
+ *    pointers that must stay valid until the call's work on `cuda_stream`
+ *    has finished; pointers named *_host are host memory.  Poses are host
+ *    memory, row-major 4x4 doubles, read during the call (copied by value).
+ *  - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).
+ *    Calls return as soon as their work is enqueued.
+ *  - Argument errors are returned synchronously and enqueue nothing.
+ *    Errors found on the device (pool or hash full, work list full) are
+ *    sticky on the map and returned by map_sync() and by every later call;
+ *    after TSDF_ERR_CAPACITY the map's contents are unspecified.  No call
+ *    aborts, traps or waits without bound.
+ *  - One map must not be used from two host threads at once.
+ *  - Voxel indexing: voxel index g = floor(p / voxel_size) per axis; block
+ *    b = floor(g / 8); local index l = g - 8 b, flattened x + 8 y + 64 z.
+ *    Block coordinates must lie in [-2^20, 2^20).
+ *  - Voxel values: D is the truncated signed distance in metres, W the
+ *    accumulated weight; W = 0 means never updated.
+ *
+ * Precision: discrete decisions (blocks met by a band segment, pixel choice,
+ * sample validity, the d_p >= -tau test, LiDAR cell choice) are taken in a
+ * prescribed FP32 operation sequence; values are accumulated in FP32 and
+ * stored in FP32 or FP16 (D / tau and W as halves).  Poses are composed in
+ * FP64 on the host and passed to the GPU as FP32, relative to the block that
+ * contains the sensor origin.
+ */
+#ifndef GB300_TSDF_H_
+#define GB300_TSDF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tsdf_map tsdf_map; /* opaque; created and owned by the library */
+
+typedef enum {
+  TSDF_OK = 0,
+  TSDF_ERR_ARG = -1,      /* bad argument: nothing was enqueued              */
+  TSDF_ERR_CUDA = -2,     /* a CUDA runtime call or launch failed             */
+  TSDF_ERR_CAPACITY = -3, /* block pool, hash table or work list full         */
+  TSDF_ERR_TIMEOUT = -4,  /* a bounded device wait gave up                    */
+  TSDF_ERR_STATE = -5     /* call not valid in the map's current state        */
+} tsdf_status;
+
+/* Pinhole intrinsics (Eq. 2): u = fu x / z + cu, v = fv y / z + cv; pixel
+ * (i, j) has its centre at (u, v) = (i, j). */
+typedef struct {
+  float fu, fv, cu, cv;
+  int32_t width, height;
+} tsdf_pinhole;
+
+/* Spinning LiDAR (Eq. 3): n_az columns cover the full azimuth circle from
+ * theta_start (radians, about +z); n_el rows cover polar angles
+ * [phi_start, phi_start + el_fov] measured from +z, row 0 first.  Ranges
+ * outside [min_range, max_range] or non-finite are invalid. */
+typedef struct {
+  int32_t n_az, n_el;
+  float theta_start, phi_start, el_fov;
+  float min_range, max_range;
+} tsdf_lidar;
+
+enum { TSDF_STORAGE_FP32 = 0, TSDF_STORAGE_FP16 = 1 };
+enum { TSDF_SENSOR_PINHOLE = 0, TSDF_SENSOR_LIDAR = 1 };
+
+/* Map options.  max_blocks: pool size in blocks (4 KiB per block in FP32,
+ * 2 KiB in FP16); hash_capacity: hash slots, rounded up to a power of two,
+ * at least 2 * max_blocks (0 = that minimum).  lidar_nearest != 0 samples
+ * LiDAR images at the nearest beam instead of guarded bilinear;
+ * lidar_guard is the bilinear foreground/background threshold in metres
+ * (<= 0: the truncation distance). */
+typedef struct {
+  int32_t storage;
+  int64_t max_blocks;
+  int64_t hash_capacity;
+  int32_t lidar_nearest;
+  float lidar_guard;
+} tsdf_map_opts;
+
+/* One frame of a batch.  `map` indexes the maps array of integrate_batch;
+ * `kind` selects which intrinsics member is read; depth_dev is the image
+ * (row-major [height][width] z-depth or [n_el][n_az] range, float32);
+ * T_world_sensor is the sensor-to-layer pose T_LC. */
+typedef struct {
+  int32_t map;
+  int32_t kind;
+  tsdf_pinhole pinhole;
+  tsdf_lidar lidar;
+  const float* depth_dev;
+  double T_world_sensor[16];
+} tsdf_frame_desc;
+
+/*
+ * map_create — an empty TSDF layer (Sec. IV-A) with voxel edge voxel_size
+ * (metres, > 0), truncation distance tau = truncation_voxels * voxel_size
+ * (the epsilon of Sec. IV-B) and weights summed up to max_weight (> 0).
+ * Defaults: FP32 storage, 2^18 blocks.  Allocates device memory on the
+ * current CUDA device.  Returns TSDF_ERR_ARG for bad sizes, TSDF_ERR_CUDA if
+ * allocation fails; *out is set only on success.
+ */
+tsdf_status map_create(float voxel_size, int32_t truncation_voxels, float max_weight,
+                       tsdf_map** out);
+
+/* map_create_ex — as map_create with explicit options (NULL = defaults). */
+tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max_weight,
+                          const tsdf_map_opts* opts, tsdf_map** out);
+
+/*
+ * integrate_depth — integrate one pinhole z-depth image (Sec. IV-B):
+ * allocate every block met by the band segment z in [d - tau, d + tau] of a
+ * valid pixel's ray (block-grid traversal after Amanatides & Woo), then for
+ * every voxel of those blocks project its centre (Eq. 1, Eq. 2), sample the
+ * nearest pixel, form d_p = d - z_v, skip the voxel if d_p < -tau, and fold
+ * min(d_p, tau) into the weighted running average with weight 1, summing
+ * weights up to max_weight.  depth_dev: float32 [height][width], z-depth in
+ * metres, <= 0 or non-finite = invalid.  T_world_cam: camera-to-layer pose
+ * (camera axes x right, y down, z forward).  Async on cuda_stream.
+ */
+tsdf_status integrate_depth(tsdf_map* map, const float* depth_dev, const tsdf_pinhole* intr,
+                            const double T_world_cam[16], void* cuda_stream);
+
+/*
+ * integrate_lidar — integrate one spinning-LiDAR range image (Sec. IV-B,
+ * Eq. 3): as integrate_depth with the band in range, d_v = |p_C| and the
+ * sample taken by bilinear interpolation between the four surrounding beam
+ * centres (azimuth wraps), skipped if any of the four is invalid or their
+ * spread exceeds the guard threshold.  range_dev: float32 [n_el][n_az].
+ */
+tsdf_status integrate_lidar(tsdf_map* map, const float* range_dev, const tsdf_lidar* intr,
+                            const double T_world_lidar[16], void* cuda_stream);
+
+/*
+ * integrate_batch — integrate n frames (any mix of sensors, sizes and maps)
+ * with one allocation launch and one integration launch.  The result equals
+ * integrating the frames one by one in array order: each map sees its frames
+ * in array order.  All maps must have been created on the current device.
+ * n <= 32 frames and at most 16 distinct maps per call.
+ */
+tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_frame_desc* frames,
+                            int32_t n, void* cuda_stream);
+
+/*
+ * query_voxels — TSDF value at n points (float32 [n][3], layer frame,
+ * metres): the voxel containing each point, looked up in the block hash.
+ * Writes dist_dev[n] and weight_dev[n]; unallocated or unobserved voxels
+ * give weight 0 and distance 0.  Async on cuda_stream.
+ */
+tsdf_status query_voxels(const tsdf_map* map, const float* pts_dev, int64_t n, float* dist_dev,
+                         float* weight_dev, void* cuda_stream);
+
+/* map_sync — wait for all work the library enqueued for this map and return
+ * its sticky device status (TSDF_OK, TSDF_ERR_CAPACITY or TSDF_ERR_TIMEOUT). */
+tsdf_status map_sync(tsdf_map* map);
+
+/* map_num_blocks — number of allocated blocks (synchronises the map). */
+tsdf_status map_num_blocks(const tsdf_map* map, int64_t* out);
+
+/* map_stats — counters since creation (synchronises): out[0] blocks
+ * allocated, out[1] voxel updates (voxel, frame pairs that passed the update
+ * test), out[2] frames integrated, out[3] sticky device status bits. */
+tsdf_status map_stats(const tsdf_map* map, int64_t out[4]);
+
+/*
+ * map_export — copy every allocated block to host memory, sorted by block
+ * coordinates (x, then y, then z): keys_host int32 [n][3], dist_host and
+ * weight_host float32 [n][512] (either may be NULL).  n must equal the block
+ * count; returns TSDF_ERR_ARG otherwise.  Synchronises.
+ */
+tsdf_status map_export(const tsdf_map* map, int32_t* keys_host, float* dist_host,
+                       float* weight_host, int64_t n);
+
+/* map_reset — drop every block (keeps the allocation), enqueued on
+ * cuda_stream; clears the sticky status. */
+tsdf_status map_reset(tsdf_map* map, void* cuda_stream);
+
+/* map_destroy — free the map's device memory (synchronises first). */
+tsdf_status map_destroy(tsdf_map* map);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_TSDF_H_ */

@@ -1,0 +1,277 @@
+"""GB300-native projective TSDF integration (nvblox, arXiv 2311.00626).
+
+Thin ctypes binding over the C ABI in ``include/tsdf.h`` (library
+``libgb300tsdf.so``, built in-tree for sm_103a by ``build.py``).  The binding
+only marshals arguments: torch CUDA tensors are passed as device pointers and
+the current torch stream as the CUDA stream; every step of the integration
+runs in the library's CUDA kernels.  There is no CPU fallback: loading fails
+loudly if the library cannot be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB, build as build_library
+
+__all__ = ["TsdfError", "Pinhole", "Lidar", "MapOpts", "FrameDesc", "TsdfMap", "lib",
+           "map_create", "map_create_ex", "integrate_depth", "integrate_lidar",
+           "integrate_batch", "query_voxels", "map_sync", "map_num_blocks", "map_stats",
+           "map_export", "map_reset", "map_destroy", "STORAGE_FP32", "STORAGE_FP16",
+           "SENSOR_PINHOLE", "SENSOR_LIDAR", "EXPORTED_SYMBOLS"]
+
+STORAGE_FP32, STORAGE_FP16 = 0, 1
+SENSOR_PINHOLE, SENSOR_LIDAR = 0, 1
+_STATUS = {0: "TSDF_OK", -1: "TSDF_ERR_ARG", -2: "TSDF_ERR_CUDA", -3: "TSDF_ERR_CAPACITY",
+           -4: "TSDF_ERR_TIMEOUT", -5: "TSDF_ERR_STATE"}
+EXPORTED_SYMBOLS = ["map_create", "map_create_ex", "integrate_depth", "integrate_lidar",
+                    "integrate_batch", "query_voxels", "map_sync", "map_num_blocks", "map_stats",
+                    "map_export", "map_reset", "map_destroy"]
+
+
+class TsdfError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {_STATUS.get(code, code)}")
+        self.code = code
+
+
+class Pinhole(ctypes.Structure):
+    _fields_ = [("fu", ctypes.c_float), ("fv", ctypes.c_float), ("cu", ctypes.c_float),
+                ("cv", ctypes.c_float), ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class Lidar(ctypes.Structure):
+    _fields_ = [("n_az", ctypes.c_int32), ("n_el", ctypes.c_int32),
+                ("theta_start", ctypes.c_float), ("phi_start", ctypes.c_float),
+                ("el_fov", ctypes.c_float), ("min_range", ctypes.c_float),
+                ("max_range", ctypes.c_float)]
+
+
+class MapOpts(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int32), ("max_blocks", ctypes.c_int64),
+                ("hash_capacity", ctypes.c_int64), ("lidar_nearest", ctypes.c_int32),
+                ("lidar_guard", ctypes.c_float)]
+
+
+class FrameDesc(ctypes.Structure):
+    _fields_ = [("map", ctypes.c_int32), ("kind", ctypes.c_int32), ("pinhole", Pinhole),
+                ("lidar", Lidar), ("depth_dev", ctypes.c_void_p),
+                ("T_world_sensor", ctypes.c_double * 16)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load (building first if stale) the CUDA library; raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build_library()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing")
+            L = ctypes.CDLL(path)
+            P, I, L64, F = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+            PP = ctypes.POINTER(ctypes.c_void_p)
+            sig = {
+                "map_create": ([F, I, F, PP], I),
+                "map_create_ex": ([F, I, F, ctypes.POINTER(MapOpts), PP], I),
+                "integrate_depth": ([P, P, ctypes.POINTER(Pinhole), P, P], I),
+                "integrate_lidar": ([P, P, ctypes.POINTER(Lidar), P, P], I),
+                "integrate_batch": ([P, I, ctypes.POINTER(FrameDesc), I, P], I),
+                "query_voxels": ([P, P, L64, P, P, P], I),
+                "map_sync": ([P], I),
+                "map_num_blocks": ([P, ctypes.POINTER(ctypes.c_int64)], I),
+                "map_stats": ([P, P], I),
+                "map_export": ([P, P, P, P, L64], I),
+                "map_reset": ([P, P], I),
+                "map_destroy": ([P], I),
+            }
+            for name, (args, res) in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise TsdfError(code, what)
+
+
+def _pose(T) -> ctypes.Array:
+    a = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(16))
+    return (ctypes.c_double * 16)(*a.tolist())
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(stream) if not hasattr(stream, "cuda_stream") else stream.cuda_stream
+
+
+def _dptr(t) -> int:
+    """Device pointer of a contiguous float32 CUDA tensor (or a raw int)."""
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def pinhole(sensor: dict) -> Pinhole:
+    return Pinhole(sensor["fu"], sensor["fv"], sensor["cu"], sensor["cv"], sensor["width"],
+                   sensor["height"])
+
+
+def lidar(sensor: dict) -> Lidar:
+    return Lidar(sensor["n_az"], sensor["n_el"], sensor["theta_start"], sensor["phi_start"],
+                 sensor["el_fov"], sensor["min_range"], sensor["max_range"])
+
+
+# ---- the C ABI under its own names -----------------------------------------------
+
+def map_create(voxel_size: float, truncation_voxels: int, max_weight: float) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().map_create(voxel_size, truncation_voxels, max_weight, ctypes.byref(h)),
+           "map_create")
+    return h.value
+
+
+def map_create_ex(voxel_size, truncation_voxels, max_weight, storage=STORAGE_FP32, max_blocks=0,
+                  hash_capacity=0, lidar_nearest=False, lidar_guard=0.0) -> int:
+    h = ctypes.c_void_p()
+    o = MapOpts(storage, max_blocks, hash_capacity, int(lidar_nearest), lidar_guard)
+    _check(lib().map_create_ex(voxel_size, truncation_voxels, max_weight, ctypes.byref(o),
+                               ctypes.byref(h)), "map_create_ex")
+    return h.value
+
+
+def integrate_depth(m: int, depth, intr: Pinhole, T_world_cam, stream=None):
+    _check(lib().integrate_depth(m, _dptr(depth), ctypes.byref(intr), _pose(T_world_cam),
+                                 _stream(stream)), "integrate_depth")
+
+
+def integrate_lidar(m: int, rng, intr: Lidar, T_world_lidar, stream=None):
+    _check(lib().integrate_lidar(m, _dptr(rng), ctypes.byref(intr), _pose(T_world_lidar),
+                                 _stream(stream)), "integrate_lidar")
+
+
+def integrate_batch(maps, frames, stream=None):
+    """maps: sequence of map handles; frames: sequence of FrameDesc."""
+    arr_m = (ctypes.c_void_p * len(maps))(*maps)
+    arr_f = (FrameDesc * len(frames))(*frames)
+    _check(lib().integrate_batch(arr_m, len(maps), arr_f, len(frames), _stream(stream)),
+           "integrate_batch")
+
+
+def query_voxels(m: int, pts, dist, weight, stream=None):
+    n = pts.shape[0] if hasattr(pts, "shape") else 0
+    _check(lib().query_voxels(m, _dptr(pts), n, _dptr(dist), _dptr(weight), _stream(stream)),
+           "query_voxels")
+
+
+def map_sync(m: int) -> int:
+    return lib().map_sync(m)
+
+
+def map_num_blocks(m: int) -> int:
+    out = ctypes.c_int64()
+    _check(lib().map_num_blocks(m, ctypes.byref(out)), "map_num_blocks")
+    return out.value
+
+
+def map_stats(m: int) -> dict:
+    out = np.zeros(4, np.int64)
+    _check(lib().map_stats(m, out.ctypes.data_as(ctypes.c_void_p)), "map_stats")
+    return {"blocks": int(out[0]), "voxel_updates": int(out[1]), "frames": int(out[2]),
+            "status_bits": int(out[3])}
+
+
+def map_export(m: int, with_values: bool = True):
+    """(keys int32[n,3] sorted by (x,y,z), D float32[n,512], W float32[n,512])."""
+    n = map_num_blocks(m)
+    keys = np.zeros((n, 3), np.int32)
+    D = np.zeros((n, 512), np.float32) if with_values else None
+    W = np.zeros((n, 512), np.float32) if with_values else None
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None  # noqa: E731
+    _check(lib().map_export(m, vp(keys), vp(D), vp(W), n), "map_export")
+    return keys, D, W
+
+
+def map_reset(m: int, stream=None):
+    _check(lib().map_reset(m, _stream(stream)), "map_reset")
+
+
+def map_destroy(m: int):
+    _check(lib().map_destroy(m), "map_destroy")
+
+
+class TsdfMap:
+    """Owning wrapper around a map handle."""
+
+    def __init__(self, voxel_size: float, truncation_voxels: int = 4, max_weight: float = 100.0,
+                 storage: int = STORAGE_FP32, max_blocks: int = 0, hash_capacity: int = 0,
+                 lidar_nearest: bool = False, lidar_guard: float = 0.0):
+        self.handle = map_create_ex(voxel_size, truncation_voxels, max_weight, storage,
+                                    max_blocks, hash_capacity, lidar_nearest, lidar_guard)
+        self.voxel_size = voxel_size
+        self.storage = storage
+
+    def integrate(self, sensor: dict, T, depth, stream=None):
+        if sensor["kind"] == "pinhole":
+            integrate_depth(self.handle, depth, pinhole(sensor), T, stream)
+        else:
+            integrate_lidar(self.handle, depth, lidar(sensor), T, stream)
+
+    def frame_desc(self, index: int, sensor: dict, T, depth) -> FrameDesc:
+        return frame_desc(index, sensor, T, depth)
+
+    def sync(self) -> int:
+        return map_sync(self.handle)
+
+    def num_blocks(self) -> int:
+        return map_num_blocks(self.handle)
+
+    def stats(self) -> dict:
+        return map_stats(self.handle)
+
+    def export(self, with_values: bool = True):
+        return map_export(self.handle, with_values)
+
+    def query(self, pts, dist, weight, stream=None):
+        query_voxels(self.handle, pts, dist, weight, stream)
+
+    def reset(self, stream=None):
+        map_reset(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            map_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def frame_desc(map_index: int, sensor: dict, T, depth) -> FrameDesc:
+    fd = FrameDesc()
+    fd.map = map_index
+    if sensor["kind"] == "pinhole":
+        fd.kind = SENSOR_PINHOLE
+        fd.pinhole = pinhole(sensor)
+    else:
+        fd.kind = SENSOR_LIDAR
+        fd.lidar = lidar(sensor)
+    fd.depth_dev = _dptr(depth)
+    fd.T_world_sensor = _pose(T)
+    return fd

@@ -1,0 +1,456 @@
+// Host side of the GB300 TSDF library: the C ABI declared in include/tsdf.h.
+//
+// Per frame the host only prepares the pose (FP64, Sec. III's T_LC inverted
+// into T_CL, anchored at the block that holds the sensor origin and rounded
+// once to FP32) and enqueues two kernels: the band allocator and the
+// per-voxel integrator (Sec. IV-B).  Nothing here touches voxel data.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "tsdf.h"
+#include "tsdf_internal.cuh"
+
+using gbt::BatchParams;
+using gbt::FrameDev;
+using gbt::MapDev;
+
+struct LidarTable {
+  int32_t n_az, n_el;
+  float theta_start, phi_start, el_fov;
+  float* dev;  // float2 [n_az] (cos, sin azimuth) then float2 [n_el] (cos, sin polar)
+};
+
+struct tsdf_map {
+  MapDev dev;
+  int device;
+  uint32_t cap;
+  int64_t max_blocks;
+  int storage;
+  float v, wmax;
+  int32_t trunc;
+  double vd, Bd;
+  int n_ctas_integrate;
+  int64_t frames;
+  unsigned long long status_seen;  // device status bits observed by the host
+  std::vector<LidarTable> tables;
+};
+
+namespace {
+
+constexpr int64_t kDefaultBlocks = 1 << 18;
+
+tsdf_status cuda_fail() {
+  cudaGetLastError();
+  return TSDF_ERR_CUDA;
+}
+
+tsdf_status status_from_bits(unsigned long long bits) {
+  if (bits & (gbt::kStPoolFull | gbt::kStHashFull | gbt::kStListFull)) return TSDF_ERR_CAPACITY;
+  if (bits & gbt::kStTimeout) return TSDF_ERR_TIMEOUT;
+  return TSDF_OK;
+}
+
+bool finite_all(const double* a, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+// T must be a rigid transform: finite, rotation block orthonormal.
+bool rigid(const double* T) {
+  if (!finite_all(T, 16)) return false;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double d = 0;
+      for (int k = 0; k < 3; ++k) d += T[4 * k + i] * T[4 * k + j];
+      if (std::fabs(d - (i == j ? 1.0 : 0.0)) > 1e-5) return false;
+    }
+  return true;
+}
+
+// Pose preparation (FP64 -> FP32), shared by both sensor kinds.  With
+// T = T_LC = [R | t]: anchor a = floor(t / B); voxel-to-sensor rotation
+// R^T and translation R^T (a B - t) in anchor-local metres; ray rotation
+// R / B and sensor origin (t - a B) / B in anchor-relative block units.
+bool prepare_pose(double Bd, const double* T, FrameDev& F) {
+  double R[3][3], t[3], e[3];
+  int64_t a[3];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) R[i][j] = T[4 * i + j];
+    t[i] = T[4 * i + 3];
+  }
+  for (int k = 0; k < 3; ++k) {
+    a[k] = (int64_t)std::floor(t[k] / Bd);
+    if (!(a[k] > -524288 && a[k] < 524288)) return false;
+    e[k] = (double)a[k] * Bd - t[k];
+  }
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) F.Rcl[3 * i + j] = (float)R[j][i];
+    F.tloc[i] = (float)((R[0][i] * e[0] + R[1][i] * e[1]) + R[2][i] * e[2]);
+    for (int j = 0; j < 3; ++j) F.M[3 * i + j] = (float)(R[i][j] / Bd);
+    F.o[i] = (float)((t[i] - (double)a[i] * Bd) / Bd);
+    F.a[i] = (int32_t)a[i];
+  }
+  return true;
+}
+
+bool valid_pinhole(const tsdf_pinhole* c) {
+  return c && c->width > 0 && c->height > 0 && (int64_t)c->width * c->height < (1ll << 30) &&
+         std::isfinite(c->fu) && std::isfinite(c->fv) && std::isfinite(c->cu) &&
+         std::isfinite(c->cv) && c->fu != 0.0f && c->fv != 0.0f;
+}
+
+bool valid_lidar(const tsdf_lidar* c) {
+  return c && c->n_az > 0 && c->n_el > 1 && (int64_t)c->n_az * c->n_el < (1ll << 30) &&
+         std::isfinite(c->theta_start) && std::isfinite(c->phi_start) &&
+         std::isfinite(c->el_fov) && c->el_fov > 0.0f && std::isfinite(c->min_range) &&
+         std::isfinite(c->max_range) && c->min_range <= c->max_range;
+}
+
+// Beam-centre direction tables of a LiDAR (Eq. 3 inverted at the cell
+// centres), computed in FP64 and rounded once; uploaded on first use.
+tsdf_status lidar_table(tsdf_map* m, const tsdf_lidar* c, const float** out) {
+  for (const LidarTable& t : m->tables)
+    if (t.n_az == c->n_az && t.n_el == c->n_el && t.theta_start == c->theta_start &&
+        t.phi_start == c->phi_start && t.el_fov == c->el_fov) {
+      *out = t.dev;
+      return TSDF_OK;
+    }
+  std::vector<float> h(2 * ((size_t)c->n_az + c->n_el));
+  for (int k = 0; k < c->n_az; ++k) {
+    const double th = (double)c->theta_start + ((double)k + 0.5) * (6.283185307179586 / (double)c->n_az);
+    h[2 * k] = (float)std::cos(th);
+    h[2 * k + 1] = (float)std::sin(th);
+  }
+  for (int j = 0; j < c->n_el; ++j) {
+    const double ph = (double)c->phi_start + ((double)j + 0.5) * ((double)c->el_fov / (double)c->n_el);
+    h[2 * (c->n_az + j)] = (float)std::cos(ph);
+    h[2 * (c->n_az + j) + 1] = (float)std::sin(ph);
+  }
+  LidarTable t{c->n_az, c->n_el, c->theta_start, c->phi_start, c->el_fov, nullptr};
+  if (cudaMalloc(&t.dev, h.size() * sizeof(float)) != cudaSuccess) return cuda_fail();
+  if (cudaMemcpy(t.dev, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(t.dev);
+    return cuda_fail();
+  }
+  m->tables.push_back(t);
+  *out = t.dev;
+  return TSDF_OK;
+}
+
+tsdf_status fill_frame(tsdf_map* m, int map_index, int kind, const tsdf_pinhole* ph,
+                       const tsdf_lidar* li, const float* depth, const double* T, FrameDev& F) {
+  std::memset(&F, 0, sizeof(F));
+  if (!depth || !T || !rigid(T)) return TSDF_ERR_ARG;
+  F.kind = kind;
+  F.map = map_index;
+  F.depth = depth;
+  if (kind == TSDF_SENSOR_PINHOLE) {
+    if (!valid_pinhole(ph)) return TSDF_ERR_ARG;
+    F.width = ph->width;
+    F.height = ph->height;
+    F.fu = ph->fu;
+    F.fv = ph->fv;
+    F.cu = ph->cu;
+    F.cv = ph->cv;
+  } else if (kind == TSDF_SENSOR_LIDAR) {
+    if (!valid_lidar(li)) return TSDF_ERR_ARG;
+    F.width = li->n_az;
+    F.height = li->n_el;
+    F.theta_start = li->theta_start;
+    F.phi_start = li->phi_start;
+    F.alpha = (float)((double)li->n_az / 6.283185307179586);  // pixels per radian
+    F.beta = (float)((double)li->n_el / (double)li->el_fov);
+    F.min_range = li->min_range;
+    F.max_range = li->max_range;
+    tsdf_status st = lidar_table(m, li, &F.tab);
+    if (st != TSDF_OK) return st;
+  } else {
+    return TSDF_ERR_ARG;
+  }
+  if (!prepare_pose(m->Bd, T, F)) return TSDF_ERR_ARG;
+  return TSDF_OK;
+}
+
+int alloc_ctas(const FrameDev& F) {
+  return (F.width * F.height + gbt::kAllocThreads - 1) / gbt::kAllocThreads;
+}
+
+bool on_device(const tsdf_map* m) {
+  int dev = -1;
+  return cudaGetDevice(&dev) == cudaSuccess && dev == m->device;
+}
+
+tsdf_status integrate_one(tsdf_map* m, int kind, const tsdf_pinhole* ph, const tsdf_lidar* li,
+                          const float* depth, const double* T, void* stream) {
+  if (!m) return TSDF_ERR_ARG;
+  if (!on_device(m)) return TSDF_ERR_STATE;
+  if (status_from_bits(m->status_seen) != TSDF_OK) return status_from_bits(m->status_seen);
+  BatchParams<1, 1> p;
+  std::memset(&p, 0, sizeof(p));
+  p.n_frames = 1;
+  p.n_maps = 1;
+  p.maps[0] = m->dev;
+  tsdf_status st = fill_frame(m, 0, kind, ph, li, depth, T, p.fr[0]);
+  if (st != TSDF_OK) return st;
+  p.fr[0].blk_begin = 0;
+  p.fr[0].bit = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (gbt::launch_band_alloc(p, alloc_ctas(p.fr[0]), s) != cudaSuccess) return cuda_fail();
+  if (gbt::launch_integrate(p, m->n_ctas_integrate, s) != cudaSuccess) return cuda_fail();
+  m->frames += 1;
+  return TSDF_OK;
+}
+
+tsdf_status read_counters(const tsdf_map* m, unsigned long long c[gbt::kNumCounters]) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail();
+  if (cudaMemcpy(c, m->dev.counters, sizeof(unsigned long long) * gbt::kNumCounters,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_fail();
+  const_cast<tsdf_map*>(m)->status_seen |= c[gbt::kCntStatus];
+  return TSDF_OK;
+}
+
+void free_map(tsdf_map* m) {
+  cudaFree(m->dev.keys);
+  cudaFree(m->dev.vals);
+  cudaFree(m->dev.mask);
+  cudaFree(m->dev.pool);
+  cudaFree(m->dev.block_keys);
+  cudaFree(m->dev.counters);
+  cudaFree(m->dev.list);
+  cudaFree(m->dev.ctl);
+  for (LidarTable& t : m->tables) cudaFree(t.dev);
+  delete m;
+}
+
+}  // namespace
+
+extern "C" {
+
+tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max_weight,
+                          const tsdf_map_opts* opts, tsdf_map** out) {
+  if (!out || !(voxel_size > 0.0f) || !std::isfinite(voxel_size) || truncation_voxels <= 0 ||
+      !(max_weight > 0.0f) || !std::isfinite(max_weight))
+    return TSDF_ERR_ARG;
+  tsdf_map_opts o{TSDF_STORAGE_FP32, kDefaultBlocks, 0, 0, 0.0f};
+  if (opts) o = *opts;
+  if (o.storage != TSDF_STORAGE_FP32 && o.storage != TSDF_STORAGE_FP16) return TSDF_ERR_ARG;
+  if (o.max_blocks <= 0) o.max_blocks = kDefaultBlocks;
+  if (o.max_blocks > (1ll << 27)) return TSDF_ERR_ARG;
+  int64_t cap = 1;
+  while (cap < std::max<int64_t>(2 * o.max_blocks, o.hash_capacity)) cap <<= 1;
+  if (cap > (1ll << 30)) return TSDF_ERR_ARG;
+
+  tsdf_map* m = new tsdf_map();
+  std::memset(&m->dev, 0, sizeof(m->dev));
+  if (cudaGetDevice(&m->device) != cudaSuccess) {
+    delete m;
+    return cuda_fail();
+  }
+  m->cap = (uint32_t)cap;
+  m->max_blocks = o.max_blocks;
+  m->storage = o.storage;
+  m->v = voxel_size;
+  m->wmax = max_weight;
+  m->trunc = truncation_voxels;
+  m->vd = (double)voxel_size;
+  m->Bd = 8.0 * m->vd;
+  m->frames = 0;
+  m->status_seen = 0;
+  MapDev& d = m->dev;
+  d.cap_mask = (uint32_t)(cap - 1);
+  d.max_blocks = (int32_t)o.max_blocks;
+  d.list_cap = (uint32_t)o.max_blocks;
+  d.storage = o.storage;
+  d.lidar_nearest = o.lidar_nearest ? 1 : 0;
+  d.v = voxel_size;
+  d.tau = (float)((double)truncation_voxels * m->vd);
+  d.inv_tau = 1.0f / d.tau;
+  d.wmax = max_weight;
+  d.guard = o.lidar_guard > 0.0f ? o.lidar_guard : d.tau;
+  const size_t voxel_bytes = o.storage == TSDF_STORAGE_FP16 ? 4 : 8;
+  bool ok = cudaMalloc(&d.keys, sizeof(unsigned long long) * cap) == cudaSuccess &&
+            cudaMalloc(&d.vals, sizeof(int32_t) * cap) == cudaSuccess &&
+            cudaMalloc(&d.mask, sizeof(uint32_t) * cap) == cudaSuccess &&
+            cudaMalloc(&d.pool, voxel_bytes * gbt::kBlockVoxels * o.max_blocks) == cudaSuccess &&
+            cudaMalloc(&d.block_keys, sizeof(unsigned long long) * o.max_blocks) == cudaSuccess &&
+            cudaMalloc(&d.counters, sizeof(unsigned long long) * gbt::kNumCounters) == cudaSuccess &&
+            cudaMalloc(&d.list, sizeof(uint32_t) * o.max_blocks) == cudaSuccess &&
+            cudaMalloc(&d.ctl, sizeof(unsigned int) * 2) == cudaSuccess;
+  if (ok) ok = gbt::launch_reset(d, m->cap, 0) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+  if (!ok) {
+    free_map(m);
+    return cuda_fail();
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+  m->n_ctas_integrate = std::max(1, sms) * gbt::integrate_ctas_per_sm(o.storage);
+  *out = m;
+  return TSDF_OK;
+}
+
+tsdf_status map_create(float voxel_size, int32_t truncation_voxels, float max_weight,
+                       tsdf_map** out) {
+  return map_create_ex(voxel_size, truncation_voxels, max_weight, nullptr, out);
+}
+
+tsdf_status integrate_depth(tsdf_map* map, const float* depth_dev, const tsdf_pinhole* intr,
+                            const double T_world_cam[16], void* cuda_stream) {
+  return integrate_one(map, TSDF_SENSOR_PINHOLE, intr, nullptr, depth_dev, T_world_cam, cuda_stream);
+}
+
+tsdf_status integrate_lidar(tsdf_map* map, const float* range_dev, const tsdf_lidar* intr,
+                            const double T_world_lidar[16], void* cuda_stream) {
+  return integrate_one(map, TSDF_SENSOR_LIDAR, nullptr, intr, range_dev, T_world_lidar, cuda_stream);
+}
+
+tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_frame_desc* frames,
+                            int32_t n, void* cuda_stream) {
+  if (!maps || !frames || n_maps <= 0 || n_maps > gbt::kMaxMaps || n <= 0 || n > gbt::kMaxFrames)
+    return TSDF_ERR_ARG;
+  for (int i = 0; i < n_maps; ++i) {
+    if (!maps[i]) return TSDF_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (maps[j] == maps[i]) return TSDF_ERR_ARG;
+    if (maps[i]->storage != maps[0]->storage) return TSDF_ERR_ARG;
+    if (!on_device(maps[i])) return TSDF_ERR_STATE;
+    if (status_from_bits(maps[i]->status_seen) != TSDF_OK) return status_from_bits(maps[i]->status_seen);
+  }
+  // the params block is large; keep it off the stack
+  static thread_local BatchParams<gbt::kMaxFrames, gbt::kMaxMaps> p;
+  std::memset(&p, 0, sizeof(p));
+  p.n_frames = n;
+  p.n_maps = n_maps;
+  int ctas = 0, integ = 1;
+  for (int i = 0; i < n_maps; ++i) {
+    p.maps[i] = maps[i]->dev;
+    integ = std::max(integ, maps[i]->n_ctas_integrate);
+  }
+  for (int f = 0; f < n; ++f) {
+    const tsdf_frame_desc& fd = frames[f];
+    if (fd.map < 0 || fd.map >= n_maps) return TSDF_ERR_ARG;
+    tsdf_status st = fill_frame(maps[fd.map], fd.map, fd.kind, &fd.pinhole, &fd.lidar,
+                                fd.depth_dev, fd.T_world_sensor, p.fr[f]);
+    if (st != TSDF_OK) return st;
+    p.fr[f].blk_begin = ctas;
+    p.fr[f].bit = f;
+    ctas += alloc_ctas(p.fr[f]);
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (gbt::launch_band_alloc(p, ctas, s) != cudaSuccess) return cuda_fail();
+  if (gbt::launch_integrate(p, integ, s) != cudaSuccess) return cuda_fail();
+  for (int f = 0; f < n; ++f) maps[frames[f].map]->frames += 1;
+  return TSDF_OK;
+}
+
+tsdf_status query_voxels(const tsdf_map* map, const float* pts_dev, int64_t n, float* dist_dev,
+                         float* weight_dev, void* cuda_stream) {
+  if (!map || n < 0 || (n > 0 && (!pts_dev || !dist_dev || !weight_dev))) return TSDF_ERR_ARG;
+  if (!on_device(map)) return TSDF_ERR_STATE;
+  if (gbt::launch_query(map->dev, pts_dev, n, dist_dev, weight_dev, (cudaStream_t)cuda_stream) !=
+      cudaSuccess)
+    return cuda_fail();
+  return TSDF_OK;
+}
+
+tsdf_status map_sync(tsdf_map* map) {
+  if (!map) return TSDF_ERR_ARG;
+  unsigned long long c[gbt::kNumCounters];
+  tsdf_status st = read_counters(map, c);
+  if (st != TSDF_OK) return st;
+  return status_from_bits(map->status_seen);
+}
+
+tsdf_status map_num_blocks(const tsdf_map* map, int64_t* out) {
+  if (!map || !out) return TSDF_ERR_ARG;
+  unsigned long long c[gbt::kNumCounters];
+  tsdf_status st = read_counters(map, c);
+  if (st != TSDF_OK) return st;
+  *out = (int64_t)std::min<unsigned long long>(c[gbt::kCntBlocks], (unsigned long long)map->max_blocks);
+  return TSDF_OK;
+}
+
+tsdf_status map_stats(const tsdf_map* map, int64_t out[4]) {
+  if (!map || !out) return TSDF_ERR_ARG;
+  unsigned long long c[gbt::kNumCounters];
+  tsdf_status st = read_counters(map, c);
+  if (st != TSDF_OK) return st;
+  out[0] = (int64_t)std::min<unsigned long long>(c[gbt::kCntBlocks], (unsigned long long)map->max_blocks);
+  out[1] = (int64_t)c[gbt::kCntUpdates];
+  out[2] = map->frames;
+  out[3] = (int64_t)map->status_seen;
+  return TSDF_OK;
+}
+
+tsdf_status map_export(const tsdf_map* map, int32_t* keys_host, float* dist_host,
+                       float* weight_host, int64_t n) {
+  if (!map || !keys_host) return TSDF_ERR_ARG;
+  int64_t nb = 0;
+  tsdf_status st = map_num_blocks(map, &nb);
+  if (st != TSDF_OK) return st;
+  if (n != nb) return TSDF_ERR_ARG;
+  if (nb == 0) return TSDF_OK;
+  std::vector<unsigned long long> bk(nb);
+  if (cudaMemcpy(bk.data(), map->dev.block_keys, sizeof(unsigned long long) * nb,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_fail();
+  const size_t voxel_bytes = map->storage == TSDF_STORAGE_FP16 ? 4 : 8;
+  std::vector<unsigned char> pool;
+  if (dist_host || weight_host) {
+    pool.resize(voxel_bytes * gbt::kBlockVoxels * nb);
+    if (cudaMemcpy(pool.data(), map->dev.pool, pool.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return cuda_fail();
+  }
+  std::vector<int64_t> order(nb);
+  std::iota(order.begin(), order.end(), 0);
+  auto coords = [&](int64_t i, int axis) { return gbt::key_coord(bk[i], axis); };
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    for (int ax = 0; ax < 3; ++ax)
+      if (coords(a, ax) != coords(b, ax)) return coords(a, ax) < coords(b, ax);
+    return false;
+  });
+  const float tau = map->dev.tau;
+  for (int64_t r = 0; r < nb; ++r) {
+    const int64_t i = order[r];
+    for (int ax = 0; ax < 3; ++ax) keys_host[3 * r + ax] = coords(i, ax);
+    if (pool.empty()) continue;
+    for (int l = 0; l < gbt::kBlockVoxels; ++l) {
+      float D, W;
+      if (map->storage == TSDF_STORAGE_FP16) {
+        const __half2 h = reinterpret_cast<const __half2*>(pool.data())[(size_t)i * 512 + l];
+        D = __low2float(h) * tau;
+        W = __high2float(h);
+      } else {
+        const float2 f = reinterpret_cast<const float2*>(pool.data())[(size_t)i * 512 + l];
+        D = f.x;
+        W = f.y;
+      }
+      if (dist_host) dist_host[(size_t)r * 512 + l] = D;
+      if (weight_host) weight_host[(size_t)r * 512 + l] = W;
+    }
+  }
+  return TSDF_OK;
+}
+
+tsdf_status map_reset(tsdf_map* map, void* cuda_stream) {
+  if (!map) return TSDF_ERR_ARG;
+  if (!on_device(map)) return TSDF_ERR_STATE;
+  if (gbt::launch_reset(map->dev, map->cap, (cudaStream_t)cuda_stream) != cudaSuccess) return cuda_fail();
+  map->status_seen = 0;
+  map->frames = 0;
+  return TSDF_OK;
+}
+
+tsdf_status map_destroy(tsdf_map* map) {
+  if (!map) return TSDF_ERR_ARG;
+  cudaDeviceSynchronize();
+  free_map(map);
+  return TSDF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// Internal device-side data layout of the GB300 TSDF library (not part of the
+// C ABI).  One map = a block hash (Sec. IV-A: integer block coordinates ->
+// 8x8x8-voxel block) plus a pool of blocks stored contiguously in HBM.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace gbt {
+
+constexpr int kBlockVoxels = 512;      // 8 x 8 x 8, x fastest
+constexpr int kMaxCells = 32;          // cap on blocks met by one band segment
+constexpr int kMaxFrames = 32;         // frames per batch (one bit each in the slot mask)
+constexpr int kMaxMaps = 16;           // maps per batch
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr int kAllocThreads = 256;     // pixels per allocation CTA
+constexpr int kIntegrateThreads = 128; // 4 voxels per thread
+
+// Per-map u64 counters.
+enum : int { kCntBlocks = 0, kCntUpdates = 1, kCntStatus = 2, kNumCounters = 4 };
+// Sticky status bits.
+enum : unsigned long long { kStPoolFull = 1, kStHashFull = 2, kStListFull = 4, kStTimeout = 8 };
+
+enum : int { kSensorPinhole = 0, kSensorLidar = 1 };
+enum : int { kStorageF32 = 0, kStorageF16 = 1 };
+
+// Device view of one map.  The work list holds the hash slots met by the
+// frames of the batch in flight; the integration launch consumes it and its
+// last CTA resets the list length.  vals[slot]: pool index >= 0; -1 = no pool block
+// (pool was full); <= -2 = block allocated by the current batch, pool index
+// -v - 2, contents not yet initialised.
+struct MapDev {
+  unsigned long long* keys;       // [cap] packed block keys, kEmptyKey = free
+  int32_t* vals;                  // [cap]
+  uint32_t* mask;                 // [cap] frames of the current batch meeting the block
+  void* pool;                     // [max_blocks][512] float2 {D, W} or __half2 {D/tau, W}
+  unsigned long long* block_keys; // [max_blocks] key of each pool block
+  unsigned long long* counters;   // [kNumCounters]
+  uint32_t* list;                 // [list_cap] slots met by the current batch
+  unsigned int* ctl;              // [0] list length, [1] finished integration CTAs
+  uint32_t list_cap;
+  uint32_t cap_mask;              // hash capacity - 1 (power of two)
+  int32_t max_blocks;
+  int32_t storage;
+  int32_t lidar_nearest;
+  float v;                        // voxel edge (m)
+  float tau;                      // truncation distance, (float)(trunc * (double)v)
+  float inv_tau;
+  float wmax;
+  float guard;                    // LiDAR bilinear guard (m)
+};
+
+// One frame as the kernels see it.  Geometry is anchor-relative: a is the
+// block holding the sensor origin; Rcl, tloc map anchor-local voxel centres
+// into the sensor frame; M, o map sensor rays into anchor-relative block
+// units.  All FP32 values are rounded once from FP64 on the host.
+struct FrameDev {
+  int32_t kind, map, width, height;
+  const float* depth;
+  const float* tab;      // LiDAR: cos/sin of beam azimuths [2*n_az], then polar [2*n_el]
+  float fu, fv, cu, cv;  // pinhole
+  float theta_start, phi_start, alpha, beta, min_range, max_range;  // LiDAR
+  float Rcl[9], tloc[3];
+  float M[9], o[3];
+  int32_t a[3];
+  int32_t blk_begin;     // first allocation CTA of this frame
+  int32_t bit;           // bit of this frame in the slot masks = its index in the batch
+};
+
+template <int NF, int NM>
+struct BatchParams {
+  int32_t n_frames;
+  int32_t n_maps;
+  MapDev maps[NM];
+  FrameDev fr[NF];
+};
+
+// Block key: three 21-bit two's-complement coordinates, x lowest.
+__host__ __device__ __forceinline__ unsigned long long pack_key(int x, int y, int z) {
+  return ((unsigned long long)(x & 0x1FFFFF)) | ((unsigned long long)(y & 0x1FFFFF) << 21) |
+         ((unsigned long long)(z & 0x1FFFFF) << 42);
+}
+__host__ __device__ __forceinline__ int key_coord(unsigned long long k, int axis) {
+  const int c = (int)((k >> (21 * axis)) & 0x1FFFFF);
+  return c >= (1 << 20) ? c - (1 << 21) : c;  // sign-extend 21 bits
+}
+// 64-bit finaliser (MurmurHash3 fmix64) for slot selection.
+__host__ __device__ __forceinline__ uint32_t hash_key(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return (uint32_t)k;
+}
+
+// Launchers (kernels.cu).
+template <int NF, int NM>
+cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, cudaStream_t s);
+template <int NF, int NM>
+cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStream_t s);
+cudaError_t launch_query(const MapDev& m, const float* pts, int64_t n, float* dist, float* weight,
+                         cudaStream_t s);
+cudaError_t launch_reset(const MapDev& m, uint32_t cap, cudaStream_t s);
+int integrate_ctas_per_sm(int storage);
+
+}  // namespace gbt

@@ -1,0 +1,66 @@
+"""Run the same frames through the oracle and through the CUDA library."""
+from __future__ import annotations
+
+import numpy as np
+
+
+def run_oracle(frames, voxel_size, trunc=4, wmax=100.0, lidar_nearest=False, guard=0.0):
+    import oracle
+    m = oracle.OracleMap(voxel_size, trunc, wmax)
+    if lidar_nearest or guard:
+        m.set_lidar_sampling(lidar_nearest, guard)
+    for f in frames:
+        m.integrate(f.sensor, f.T, f.depth)
+    out = m.export()
+    counters = m.counters()
+    m.close()
+    return out, counters
+
+
+def to_device(frames):
+    import torch
+    return [torch.from_numpy(np.ascontiguousarray(f.depth)).cuda() for f in frames]
+
+
+def run_gpu(frames, voxel_size, trunc=4, wmax=100.0, storage=0, batch=1, lidar_nearest=False,
+            guard=0.0, max_blocks=0, keep=False):
+    """Integrate `frames` (in order) into a fresh map, `batch` frames per
+    integrate_batch call (batch=1: integrate_depth / integrate_lidar)."""
+    import torch
+    import paper_2311_00626_gb300 as gt
+    m = gt.TsdfMap(voxel_size, trunc, wmax, storage=storage, max_blocks=max_blocks,
+                   lidar_nearest=lidar_nearest, lidar_guard=guard)
+    dev = to_device(frames)
+    if batch == 1:
+        for f, d in zip(frames, dev):
+            m.integrate(f.sensor, f.T, d)
+    else:
+        for s in range(0, len(frames), batch):
+            descs = [gt.frame_desc(0, f.sensor, f.T, d)
+                     for f, d in zip(frames[s:s + batch], dev[s:s + batch])]
+            gt.integrate_batch([m.handle], descs)
+    torch.cuda.synchronize()
+    status = m.sync()
+    out = m.export()
+    stats = m.stats()
+    if keep:
+        return out, stats, status, m
+    m.close()
+    return out, stats, status
+
+
+def compare(gpu, orc, tol_d, label=""):
+    """Block set and weights bit-exact; distances within tol_d (metres)
+    wherever the oracle's weight is nonzero; untouched voxels hold zeros."""
+    gk, gD, gW = gpu
+    ok, oD, oW = orc
+    assert gk.shape == ok.shape, f"{label}: {len(gk)} blocks on the GPU, {len(ok)} in the oracle"
+    np.testing.assert_array_equal(gk, ok, err_msg=f"{label}: block sets differ")
+    bad = np.count_nonzero(gW.astype(np.float64) != oW)
+    assert bad == 0, f"{label}: {bad} voxel weights differ"
+    obs = oW > 0
+    err = np.abs(gD[obs].astype(np.float64) - oD[obs]) if obs.any() else np.zeros(1)
+    assert err.max() <= tol_d, f"{label}: max |dD| {err.max():.3e} > {tol_d:.3e}"
+    assert np.all(gD[~obs] == 0)
+    return {"blocks": len(gk), "observed": int(obs.sum()), "max_err": float(err.max()),
+            "rms_err": float(np.sqrt(np.mean(err ** 2)))}

@@ -1,0 +1,306 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Block sets and per-voxel weights must match bit-exactly; distances must lie
+within 1e-4 voxel sizes for FP32 storage (pinhole).  LiDAR values carry the
+FP32 error of ranges up to tens of metres (range and bilinear sample in
+FP32), so their bound adds 4 ulp of the largest range to 1e-4 voxel sizes.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from synth.configs import Frame
+from tests.runners import compare, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+REPORT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+
+
+def _record(name, stats):
+    if os.path.isdir(REPORT):
+        with open(os.path.join(REPORT, "parity_errors.jsonl"), "a") as fh:
+            fh.write(json.dumps({"case": name, **stats}) + "\n")
+
+
+def tol_pinhole(v):
+    return 1e-4 * float(np.float32(v))
+
+
+def tol_lidar(v, r_max):
+    return 1e-4 * float(np.float32(v)) + 4 * float(np.spacing(np.float32(r_max)))
+
+
+def _rot(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    a, b, c, d = q
+    return np.array([[a*a+b*b-c*c-d*d, 2*(b*c-a*d), 2*(b*d+a*c)],
+                     [2*(b*c+a*d), a*a-b*b+c*c-d*d, 2*(c*d-a*b)],
+                     [2*(b*d-a*c), 2*(c*d+a*b), a*a-b*b-c*c+d*d]])
+
+
+def _parity(name, frames, v, tol, **kw):
+    orc, oc = run_oracle(frames, v, lidar_nearest=kw.get("lidar_nearest", False),
+                         guard=kw.get("guard", 0.0))
+    gpu, gs, status = run_gpu(frames, v, **kw)
+    assert status == 0, f"device status {status}"
+    st = compare(gpu, orc, tol, name)
+    assert gs["voxel_updates"] == oc["total_updates"], (gs, oc)
+    _record(name, st)
+    return st
+
+
+# ------------------------------------------------------------------ pinhole
+
+def test_tiny_plane_sphere():
+    w = synth.config_tiny()
+    st = _parity("tiny", w.frames, w.voxel_size, tol_pinhole(w.voxel_size))
+    assert st["blocks"] > 50
+
+
+@pytest.mark.parametrize("seed,origin", [(1, (103.7, -52.1, 7.3)), (3, (-2001.13, 17.9, -3.31))])
+def test_tilted_plane_far_pose(seed, origin):
+    rng = np.random.default_rng(seed)
+    R = _rot(rng)
+    T = np.eye(4)
+    T[:3, :3] = R
+    T[:3, 3] = origin
+    n = R[:, 2] + 0.4 * rng.normal(size=3)
+    n /= np.linalg.norm(n)
+    c = float(n @ (T[:3, 3] + 1.7 * R[:, 2]))
+    cam = synth.pinhole(40, 30, 30.0)
+    prims = synth.scene(synth.prim(synth.PLANE, *n, c))
+    d = synth.render_pinhole(prims, T, cam["fu"], cam["fv"], cam["cu"], cam["cv"], 40, 30,
+                             max_depth=6.0)
+    _parity(f"tilted{seed}", [Frame(cam, T, d)], 0.05, tol_pinhole(0.05))
+
+
+def test_room_frames_640x480():
+    """Twelve full-size frames of the room sequence (several thousand blocks,
+    many CTAs and warps per frame, ragged last CTA of pixels)."""
+    w = synth.config_room(n_frames=300)
+    frames = w.frames[:12]
+    st = _parity("room12", frames, w.voxel_size, tol_pinhole(w.voxel_size))
+    assert st["blocks"] > 2000
+
+
+@pytest.mark.parametrize("W,H", [(37, 23), (1, 1), (333, 7)])
+def test_ragged_image_sizes(W, H):
+    prims = synth.room_scene(3)
+    Ts = synth.trajectory(3, prims, 4)
+    cam = synth.pinhole(W, H, 0.8 * max(W, H))
+    frames = [Frame(cam, T, synth.render_frame(prims, cam, T, synth.configs.ROOM_NOISE, 3, i))
+              for i, T in enumerate(Ts)]
+    _parity(f"ragged{W}x{H}", frames, 0.04, tol_pinhole(0.04))
+
+
+def test_invalid_and_empty_frames():
+    """Non-finite, negative and zero depths are invalid; an all-invalid frame
+    allocates nothing."""
+    cam = synth.pinhole(64, 48, 50.0, 32.0, 24.0)
+    rng = np.random.default_rng(1)
+    d = rng.uniform(0.5, 3.0, (48, 64)).astype(np.float32)
+    d[rng.uniform(size=d.shape) < 0.3] = np.nan
+    d[rng.uniform(size=d.shape) < 0.1] = np.inf
+    d[rng.uniform(size=d.shape) < 0.1] = -1.0
+    empty = np.zeros((48, 64), np.float32)
+    frames = [Frame(cam, np.eye(4), empty), Frame(cam, np.eye(4), d)]
+    _parity("invalid", frames, 0.05, tol_pinhole(0.05))
+    gpu, gs, status = run_gpu([frames[0]], 0.05)
+    assert status == 0 and len(gpu[0]) == 0 and gs["voxel_updates"] == 0
+
+
+def test_weight_cap_repeated_frame():
+    """150 repetitions of one frame: weights saturate at max_weight = 100."""
+    w = synth.config_tiny()
+    frames = w.frames * 150
+    _parity("repeat150", frames, w.voxel_size, tol_pinhole(w.voxel_size))
+    gpu, _, _ = run_gpu(frames, w.voxel_size)
+    assert set(np.unique(gpu[2]).tolist()) <= {0.0, 100.0}
+
+
+def test_batched_equals_sequential_and_oracle():
+    """integrate_batch with 8 frames per launch gives the same map, bit for
+    bit, as one frame per launch, and matches the oracle."""
+    w = synth.config_room(n_frames=300)
+    frames = w.frames[40:64]
+    seq, _, _ = run_gpu(frames, w.voxel_size)
+    bat, _, st = run_gpu(frames, w.voxel_size, batch=8)
+    assert st == 0
+    for a, b in zip(seq, bat):
+        np.testing.assert_array_equal(a, b)
+    orc, _ = run_oracle(frames, w.voxel_size)
+    _record("batched8", compare(bat, orc, tol_pinhole(w.voxel_size), "batched8"))
+
+
+def test_multi_map_batch():
+    """One launch over three maps with different voxel sizes and interleaved
+    frames: each map equals its own one-frame-per-launch result."""
+    import paper_2311_00626_gb300 as gt
+    from tests.runners import to_device
+    sizes = [0.02, 0.05, 0.1]
+    seqs = []
+    for k in range(3):
+        prims = synth.room_scene(50 + k)
+        Ts = synth.trajectory(50 + k, prims, 6)
+        cam = synth.configs.SERVING_SENSORS[k]
+        seqs.append([Frame(cam, T, synth.render_frame(prims, cam, T, synth.configs.ROOM_NOISE,
+                                                      50 + k, i)) for i, T in enumerate(Ts)])
+    maps = [gt.TsdfMap(v) for v in sizes]
+    order = [(k, i) for i in range(6) for k in range(3)]
+    devs = {(k, i): to_device([seqs[k][i]])[0] for k, i in order}
+    for s in range(0, len(order), 9):
+        chunk = order[s:s + 9]
+        descs = [gt.frame_desc(k, seqs[k][i].sensor, seqs[k][i].T, devs[(k, i)]) for k, i in chunk]
+        gt.integrate_batch([m.handle for m in maps], descs)
+    torch.cuda.synchronize()
+    for k in range(3):
+        assert maps[k].sync() == 0
+        got = maps[k].export()
+        ref, _, _ = run_gpu(seqs[k], sizes[k])
+        for a, b in zip(got, ref):
+            np.testing.assert_array_equal(a, b)
+        orc, _ = run_oracle(seqs[k], sizes[k])
+        compare(got, orc, tol_pinhole(sizes[k]), f"multimap{k}")
+        maps[k].close()
+
+
+def test_query_voxels_matches_export():
+    import paper_2311_00626_gb300 as gt
+    w = synth.config_tiny()
+    (keys, D, W), _, _, m = run_gpu(w.frames, w.voxel_size, keep=True)
+    v = float(np.float32(w.voxel_size))
+    rng = np.random.default_rng(0)
+    bi = rng.integers(0, len(keys), 4000)
+    li = rng.integers(0, 512, 4000)
+    loc = np.stack([li % 8, (li // 8) % 8, li // 64], 1)
+    g = keys[bi].astype(np.int64) * 8 + loc
+    pts = ((g + rng.uniform(0.2, 0.8, g.shape)) * v).astype(np.float32)
+    far = np.array([[100.0, 100.0, 100.0], [-50.0, 3.0, 2.0]], np.float32)
+    P = torch.from_numpy(np.concatenate([pts, far])).cuda()
+    dist = torch.empty(len(P), device="cuda")
+    wt = torch.empty(len(P), device="cuda")
+    m.query(P, dist, wt)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(dist.cpu().numpy()[:4000], D[bi, li])
+    np.testing.assert_array_equal(wt.cpu().numpy()[:4000], W[bi, li])
+    assert np.all(wt.cpu().numpy()[4000:] == 0)
+    m.close()
+
+
+def test_capacity_error_is_reported():
+    """A pool too small for the frame: map_sync reports TSDF_ERR_CAPACITY and
+    later integrations are refused with the same status."""
+    import paper_2311_00626_gb300 as gt
+    w = synth.config_tiny()
+    m = gt.TsdfMap(w.voxel_size, max_blocks=16)
+    d = torch.from_numpy(w.frames[0].depth).cuda()
+    m.integrate(w.frames[0].sensor, w.frames[0].T, d)
+    assert m.sync() == -3
+    with pytest.raises(gt.TsdfError):
+        m.integrate(w.frames[0].sensor, w.frames[0].T, d)
+    m.reset()
+    torch.cuda.synchronize()
+    assert m.sync() == 0
+    m.close()
+
+
+def test_argument_errors():
+    import paper_2311_00626_gb300 as gt
+    with pytest.raises(gt.TsdfError):
+        gt.map_create(-1.0, 4, 100.0)
+    m = gt.TsdfMap(0.05)
+    cam = synth.pinhole(64, 48, 50.0)
+    d = torch.zeros((48, 64), device="cuda")
+    bad = np.eye(4)
+    bad[0, 0] = 2.0  # not a rotation
+    with pytest.raises(gt.TsdfError):
+        m.integrate(cam, bad, d)
+    with pytest.raises(gt.TsdfError):
+        gt.integrate_depth(m.handle, 0, gt.pinhole(cam), np.eye(4))
+    m.close()
+
+
+def test_reset_then_reintegrate_is_identical():
+    import paper_2311_00626_gb300 as gt
+    w = synth.config_room(n_frames=300)
+    frames = w.frames[:3]
+    (a, _, _, m) = run_gpu(frames, w.voxel_size, keep=True)
+    m.reset()
+    from tests.runners import to_device
+    for f, d in zip(frames, to_device(frames)):
+        m.integrate(f.sensor, f.T, d)
+    torch.cuda.synchronize()
+    b = m.export()
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    m.close()
+
+
+# -------------------------------------------------------------------- LiDAR
+
+def _lidar_pose(seed):
+    rng = np.random.default_rng(seed)
+    T = np.eye(4)
+    T[:3, :3] = _rot(rng)
+    T[:3, 3] = rng.uniform(-50, 50, 3)
+    return T
+
+
+def test_lidar_inside_sphere():
+    lid = synth.lidar64(n_az=128, n_el=16)
+    img = np.full((16, 128), 10.0, np.float32)
+    _parity("lidar_sphere", [Frame(lid, _lidar_pose(3), img)], 0.05, tol_lidar(0.05, 10.0))
+
+
+def test_lidar_wrap_and_guard():
+    lid = synth.lidar64(n_az=96, n_el=12)
+    th = lid["theta_start"] + (np.arange(96) + 0.5) * 2 * math.pi / 96
+    img = (8.0 + 0.06 * np.sin(th)[None, :] + 0.01 * np.arange(12)[:, None]).astype(np.float32)
+    img[:, 20:40] += 3.0
+    frames = [Frame(lid, _lidar_pose(4), img), Frame(lid, _lidar_pose(4), img)]
+    _parity("lidar_wrap_guard", frames, 0.05, tol_lidar(0.05, 12.0))
+
+
+def test_lidar_nearest_mode():
+    lid = synth.lidar64(n_az=64, n_el=8)
+    rng = np.random.default_rng(0)
+    img = rng.uniform(5.0, 5.1, (8, 64)).astype(np.float32)
+    _parity("lidar_nearest", [Frame(lid, _lidar_pose(6), img)], 0.05, tol_lidar(0.05, 5.1),
+            lidar_nearest=True)
+
+
+def test_lidar_outdoor_full_scan():
+    """A full 1024x64 scan (0.5-30 m, noisy) of the seeded outdoor scene."""
+    prims = synth.outdoor_scene(4)
+    Ts = synth.trajectory(4, prims, 3, xy=(4.0, 36.0))
+    lid = synth.lidar64()
+    frames = []
+    for i, T in enumerate(Ts):
+        TL = synth.configs.rig_poses(T)[4]
+        frames.append(Frame(lid, TL, synth.render_frame(prims, lid, TL, {"sigma": 0.02}, 4, i)))
+    _parity("lidar_outdoor", frames, 0.05, tol_lidar(0.05, 30.0))
+
+
+def test_rig_mixed_sensors_batched():
+    """One step of the rig (four pinholes of three sizes plus the LiDAR) as a
+    single batch equals the frames integrated one by one, and the oracle."""
+    w = synth.config_rig(n_steps=2)
+    seq, _, _ = run_gpu(w.frames, w.voxel_size)
+    bat, _, st = run_gpu(w.frames, w.voxel_size, batch=5)
+    assert st == 0
+    for a, b in zip(seq, bat):
+        np.testing.assert_array_equal(a, b)
+    orc, _ = run_oracle(w.frames, w.voxel_size)
+    _record("rig2", compare(bat, orc, tol_lidar(w.voxel_size, 30.0), "rig2"))
