@@ -1,0 +1,361 @@
+"""Benchmark: projective TSDF integration of the 640x480 room sequence.
+
+Workload: the seeded 10x10x3 m room, 300 frames of 640x480 float32 depth
+(f = 525, noise N(0, (0.0012 z^2)^2), 5 % invalid pixels, depth > 5 m
+invalid), voxel 0.02 m, truncation 4 voxels, max weight 100, FP32 storage.
+One step = every step of the integration path over the whole sequence into a
+freshly reset map: band-segment block allocation in the GPU hash, then the
+per-voxel projective TSDF update, frames batched `--batch` per launch.
+
+Prints one JSON line (rank 0).  `value` is voxel updates per second over all
+ranks (each rank integrates its own replica: the path shards by map, no
+collective); `e2e` repeats the measurement with depth frames copied from
+pinned host memory inside the timed region.  `--impl reference` times the
+CPU oracle (test infrastructure, FP64) on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "TSDF voxel updates/s and frames/s (640x480, 2 cm); % HBM peak; p99 latency"
+UNIT = "voxel updates/s"
+WORKLOAD = "room 10x10x3 m, 300 frames 640x480 f=525, voxel 0.02 m, trunc 4 voxels, max weight 100"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reference_arm(args):
+    """Time the CPU oracle on a bounded sample of the workload (rank 0)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    w = synth.config_room(n_frames=300)
+    # size the per-step sample so that warm-up plus timed steps take about
+    # two minutes of host time
+    probe = oracle.OracleMap(w.voxel_size, w.truncation_voxels, w.max_weight)
+    t0 = time.perf_counter()
+    for f in w.frames[:10]:
+        probe.integrate(f.sensor, f.T, f.depth)
+    per_frame = (time.perf_counter() - t0) / 10
+    probe.close()
+    n = int(min(300, max(10, 120.0 / ((args.warmup + args.steps) * per_frame))))
+    per_step = []
+    updates = 0
+    for step in range(args.warmup + args.steps):
+        m = oracle.OracleMap(w.voxel_size, w.truncation_voxels, w.max_weight)
+        t0 = time.perf_counter()
+        for f in w.frames[:n]:
+            m.integrate(f.sensor, f.T, f.depth)
+        dt = time.perf_counter() - t0
+        updates = m.counters()["total_updates"]
+        m.close()
+        if step >= args.warmup:
+            per_step.append(dt)
+    sec = sum(per_step)
+    value = updates * len(per_step) / sec
+    cores = os.cpu_count()
+    sample = f"first {n} of 300 frames per step (oracle, FP64, OpenMP over blocks)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sec / len(per_step), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_frames": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "frames_per_s": n * len(per_step) / sec}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(frames_n: int):
+    import oracle
+    import synth
+    w = synth.config_room(n_frames=300)
+    m = oracle.OracleMap(w.voxel_size, w.truncation_voxels, w.max_weight)
+    t0 = time.perf_counter()
+    for f in w.frames[:frames_n]:
+        m.integrate(f.sensor, f.T, f.depth)
+    dt = time.perf_counter() - t0
+    upd = m.counters()["total_updates"]
+    m.close()
+    return {"value": upd / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {frames_n} of the 300 frames, one pass ({dt:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=8, help="frames per integrate_batch launch")
+    ap.add_argument("--ref-frames", type=int, default=150)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    ws, rank, local = _dist()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2311_00626_gb300 as gt
+    import synth
+    w = synth.config_room(n_frames=300)
+    n_frames = len(w.frames)
+    host = torch.from_numpy(np.stack([f.depth for f in w.frames])).pin_memory()
+    dev = host.to("cuda", non_blocking=False)
+    frames_dev = [dev[i] for i in range(n_frames)]
+    in_bytes = host.numel() * 4
+
+    def make_step(m, batch):
+        descs = [gt.frame_desc(0, f.sensor, f.T, d) for f, d in zip(w.frames, frames_dev)]
+
+        def step():
+            m.reset()
+            if batch == 1:
+                for f, d in zip(w.frames, frames_dev):
+                    m.integrate(f.sensor, f.T, d)
+            else:
+                for s in range(0, n_frames, batch):
+                    gt.integrate_batch([m.handle], descs[s:s + batch])
+        return step
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(step, k):
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / k
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # ---- headline: FP32 storage, batched launches
+    m = gt.TsdfMap(w.voxel_size, w.truncation_voxels, w.max_weight, storage=gt.STORAGE_FP32)
+    step = make_step(m, args.batch)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = m.stats()
+    updates_per_step = st["voxel_updates"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    gt.map_timing(m.handle, True)
+    ms = timed(step, args.steps)
+    alloc_ms, integ_ms, calls = gt.map_kernel_times(m.handle)
+    gt.map_timing(m.handle, False)
+    clk = clocks.stop()
+    st = m.stats()
+    assert st["voxel_updates"] == updates_per_step, "non-deterministic update count"
+    launches_per_step = st["launches"]
+    visits = st["block_visits"]
+    fresh = st["blocks"]
+    # algorithmic bytes of one integration launch: every listed block read and
+    # written once (fresh blocks only written), plus the depth images it reads
+    block_bytes = 512 * 8
+    bytes_per_step = (2 * visits - fresh) * block_bytes + in_bytes
+    integ_bytes_per_launch = bytes_per_step / launches_per_step
+    integ_ms_per_launch = integ_ms / max(calls, 1)
+    hbm_peak, peak_src = _peaks()
+    achieved = integ_bytes_per_launch / (integ_ms_per_launch * 1e-3) / 1e9
+    value = ws * updates_per_step / (ms * 1e-3)
+    fps = ws * n_frames / (ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers
+    e2e_step_inner = make_step(m, args.batch)
+    host_res = torch.zeros(6, dtype=torch.int64)
+
+    def e2e_step():
+        dev.copy_(host, non_blocking=True)
+        e2e_step_inner()
+        s = m.stats()  # device -> host read of the step's result (synchronises)
+        host_res[1] = s["voxel_updates"]
+
+    k_e2e = max(1, min(args.steps, 10))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / k_e2e
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    forms = {}
+    if not args.no_forms:
+        # plain form: one frame per launch, FP32; per-frame latency from events
+        m1 = gt.TsdfMap(w.voxel_size, w.truncation_voxels, w.max_weight)
+        s1 = make_step(m1, 1)
+        for _ in range(args.warmup):
+            s1()
+        ms1 = timed(s1, max(3, args.steps // 2))
+        lat = []
+        m1.reset()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(n_frames)]
+        for (a, b), f, d in zip(evs, w.frames, frames_dev):
+            a.record()
+            m1.integrate(f.sensor, f.T, d)
+            b.record()
+        torch.cuda.synchronize()
+        lat = sorted(a.elapsed_time(b) for a, b in evs)
+        forms["fp32_one_frame_per_launch"] = {
+            "ms_per_step": ms1, "voxel_updates_per_s": ws * updates_per_step / (ms1 * 1e-3),
+            "frames_per_s": ws * n_frames / (ms1 * 1e-3),
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[int(0.99 * (len(lat) - 1))]}}
+        m1.close()
+        # batched FP16 storage (precision pattern)
+        m2 = gt.TsdfMap(w.voxel_size, w.truncation_voxels, w.max_weight, storage=gt.STORAGE_FP16)
+        s2 = make_step(m2, args.batch)
+        for _ in range(args.warmup):
+            s2()
+        ms2 = timed(s2, args.steps)
+        forms[f"fp16_batched_{args.batch}"] = {
+            "ms_per_step": ms2, "voxel_updates_per_s": ws * updates_per_step / (ms2 * 1e-3),
+            "frames_per_s": ws * n_frames / (ms2 * 1e-3)}
+        m2.close()
+        forms["fp32_batched_speedup_vs_one_frame"] = ms1 / ms
+        forms["fp16_batched_speedup_vs_one_frame"] = ms1 / ms2
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.ref_frames)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "storage": "fp32", "frames_per_launch": args.batch,
+                       "frames_per_step": n_frames, "voxel_updates_per_step": updates_per_step,
+                       "l2": f"inputs {in_bytes / 1e6:.0f} MB resident in HBM (> 129 MB L2)",
+                       "parallelism": f"replicas x{ws}"},
+            "frames_per_s": fps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "kernel": "integrate_kernel", "peak_source": peak_src,
+                         "bytes_per_launch": integ_bytes_per_launch,
+                         "ms_per_launch": integ_ms_per_launch,
+                         "alloc_ms_per_launch": alloc_ms / max(calls, 1)},
+            "kernel_ms_per_step": {"band_alloc": alloc_ms / args.steps,
+                                   "integrate": integ_ms / args.steps},
+            "e2e": {"value": ws * updates_per_step / (e2e_ms * 1e-3), "unit": UNIT,
+                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": in_bytes,
+                    "d2h_bytes_per_step": 48},
+            "gpu_launches": args.steps * (1 + 2 * launches_per_step),
+            "clocks": clk,
+            "forms": forms,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    m.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -169,10 +169,23 @@ tsdf_status map_sync(tsdf_map* map);
 /* map_num_blocks — number of allocated blocks (synchronises the map). */
 tsdf_status map_num_blocks(const tsdf_map* map, int64_t* out);
 
-/* map_stats — counters since creation (synchronises): out[0] blocks
- * allocated, out[1] voxel updates (voxel, frame pairs that passed the update
- * test), out[2] frames integrated, out[3] sticky device status bits. */
-tsdf_status map_stats(const tsdf_map* map, int64_t out[4]);
+/* map_stats — counters since creation or the last map_reset (synchronises):
+ * out[0] blocks allocated, out[1] voxel updates (voxel, frame pairs that
+ * passed the update test), out[2] frames integrated, out[3] sticky device
+ * status bits, out[4] block visits (blocks listed by integration launches,
+ * summed over launches), out[5] integration launches. */
+tsdf_status map_stats(const tsdf_map* map, int64_t out[6]);
+
+/* map_timing — diagnostics: while enabled, every integrate call on this map
+ * (or integrate_batch whose first map it is) records CUDA events around its
+ * allocation and integration kernels, for up to 4096 calls.  Enabling creates
+ * the events; call it outside any timed region. */
+tsdf_status map_timing(tsdf_map* map, int32_t enable);
+
+/* map_kernel_times — waits for the recorded calls and returns the summed
+ * device time of their allocation (out_ms[0]) and integration (out_ms[1])
+ * kernels and the number of calls recorded; then clears the record. */
+tsdf_status map_kernel_times(tsdf_map* map, double out_ms[2], int64_t* calls);
 
 /*
  * map_export — copy every allocated block to host memory, sorted by block

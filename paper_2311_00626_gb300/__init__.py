@@ -20,7 +20,8 @@ from .build import LIB, build as build_library
 __all__ = ["TsdfError", "Pinhole", "Lidar", "MapOpts", "FrameDesc", "TsdfMap", "lib",
            "map_create", "map_create_ex", "integrate_depth", "integrate_lidar",
            "integrate_batch", "query_voxels", "map_sync", "map_num_blocks", "map_stats",
-           "map_export", "map_reset", "map_destroy", "STORAGE_FP32", "STORAGE_FP16",
+           "map_export", "map_reset", "map_destroy", "map_timing", "map_kernel_times",
+           "STORAGE_FP32", "STORAGE_FP16",
            "SENSOR_PINHOLE", "SENSOR_LIDAR", "EXPORTED_SYMBOLS"]
 
 STORAGE_FP32, STORAGE_FP16 = 0, 1
@@ -29,7 +30,7 @@ _STATUS = {0: "TSDF_OK", -1: "TSDF_ERR_ARG", -2: "TSDF_ERR_CUDA", -3: "TSDF_ERR_
            -4: "TSDF_ERR_TIMEOUT", -5: "TSDF_ERR_STATE"}
 EXPORTED_SYMBOLS = ["map_create", "map_create_ex", "integrate_depth", "integrate_lidar",
                     "integrate_batch", "query_voxels", "map_sync", "map_num_blocks", "map_stats",
-                    "map_export", "map_reset", "map_destroy"]
+                    "map_export", "map_reset", "map_destroy", "map_timing", "map_kernel_times"]
 
 
 class TsdfError(RuntimeError):
@@ -90,6 +91,8 @@ def lib():
                 "map_export": ([P, P, P, P, L64], I),
                 "map_reset": ([P, P], I),
                 "map_destroy": ([P], I),
+                "map_timing": ([P, I], I),
+                "map_kernel_times": ([P, P, ctypes.POINTER(ctypes.c_int64)], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -188,10 +191,23 @@ def map_num_blocks(m: int) -> int:
 
 
 def map_stats(m: int) -> dict:
-    out = np.zeros(4, np.int64)
+    out = np.zeros(6, np.int64)
     _check(lib().map_stats(m, out.ctypes.data_as(ctypes.c_void_p)), "map_stats")
     return {"blocks": int(out[0]), "voxel_updates": int(out[1]), "frames": int(out[2]),
-            "status_bits": int(out[3])}
+            "status_bits": int(out[3]), "block_visits": int(out[4]), "launches": int(out[5])}
+
+
+def map_timing(m: int, enable: bool = True):
+    _check(lib().map_timing(m, int(enable)), "map_timing")
+
+
+def map_kernel_times(m: int):
+    """(alloc_ms, integrate_ms, calls) summed over the recorded calls."""
+    out = np.zeros(2, np.float64)
+    calls = ctypes.c_int64()
+    _check(lib().map_kernel_times(m, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(calls)),
+           "map_kernel_times")
+    return float(out[0]), float(out[1]), int(calls.value)
 
 
 def map_export(m: int, with_values: bool = True):

@@ -32,17 +32,15 @@ constexpr float kHalfPiF = (float)(3.14159265358979323846 / 2);
 __device__ __forceinline__ int hash_insert(const MapDev& m, unsigned long long key, bool& inserted) {
   uint32_t slot = hash_key(key) & m.cap_mask;
   inserted = false;
+  // one atomic per probed slot: it inserts into an empty slot and reports
+  // the slot's key otherwise (a single L2 round trip when the key is found)
   for (uint32_t probe = 0; probe <= m.cap_mask; ++probe) {
-    const unsigned long long k = __ldcg(m.keys + slot);
-    if (k == key) return (int)slot;
-    if (k == kEmptyKey) {
-      const unsigned long long old = atomicCAS(m.keys + slot, kEmptyKey, key);
-      if (old == kEmptyKey) {
-        inserted = true;
-        return (int)slot;
-      }
-      if (old == key) return (int)slot;
+    const unsigned long long old = atomicCAS(m.keys + slot, kEmptyKey, key);
+    if (old == kEmptyKey) {
+      inserted = true;
+      return (int)slot;
     }
+    if (old == key) return (int)slot;
     slot = (slot + 1) & m.cap_mask;
   }
   return -1;
@@ -61,61 +59,6 @@ __device__ __forceinline__ int hash_find(const MapDev& m, unsigned long long key
 
 // ------------------------------------------------- block-grid traversal
 
-// Walk of a segment o + s dir, s in [s0, s1] (block units, anchor-relative)
-// through the block grid: crossing parameters are recomputed from the origin
-// at every step, ties between axes go to x, then y, then z; at most
-// kMaxCells cells.
-struct Walk {
-  int cx, cy, cz;
-  int sx, sy, sz;
-  float ix, iy, iz;
-  float tx, ty, tz;
-  float s1;
-  int n;
-
-  __device__ __forceinline__ static float cross(int c, int step, float o, float inv) {
-    if (step == 0) return __int_as_float(0x7f800000);  // +inf
-    const float bnd = (float)(step > 0 ? c + 1 : c);
-    return __fmul_rn(__fsub_rn(bnd, o), inv);
-  }
-  __device__ __forceinline__ static int sgn(float d) { return d > 0.0f ? 1 : (d < 0.0f ? -1 : 0); }
-
-  // false if the segment starts outside the 21-bit key range
-  __device__ __forceinline__ bool start(const float* o, float dx, float dy, float dz, float s0,
-                                        float s1_) {
-    const float px = __fmaf_rn(s0, dx, o[0]), py = __fmaf_rn(s0, dy, o[1]), pz = __fmaf_rn(s0, dz, o[2]);
-    if (!(fabsf(px) < 262144.0f && fabsf(py) < 262144.0f && fabsf(pz) < 262144.0f)) return false;
-    cx = (int)floorf(px);
-    cy = (int)floorf(py);
-    cz = (int)floorf(pz);
-    sx = sgn(dx);
-    sy = sgn(dy);
-    sz = sgn(dz);
-    ix = sx ? __frcp_rn(dx) : 0.0f;
-    iy = sy ? __frcp_rn(dy) : 0.0f;
-    iz = sz ? __frcp_rn(dz) : 0.0f;
-    tx = cross(cx, sx, o[0], ix);
-    ty = cross(cy, sy, o[1], iy);
-    tz = cross(cz, sz, o[2], iz);
-    s1 = s1_;
-    n = 1;
-    return true;
-  }
-  // advance to the next cell; false when the segment ends
-  __device__ __forceinline__ bool next(const float* o) {
-    int k = 0;
-    float t = tx;
-    if (ty < t) { k = 1; t = ty; }
-    if (tz < t) { k = 2; t = tz; }
-    if (!(t <= s1) || n == kMaxCells) return false;
-    if (k == 0) { cx += sx; tx = cross(cx, sx, o[0], ix); }
-    else if (k == 1) { cy += sy; ty = cross(cy, sy, o[1], iy); }
-    else { cz += sz; tz = cross(cz, sz, o[2], iz); }
-    ++n;
-    return true;
-  }
-};
-
 __device__ __forceinline__ void claim_block(const MapDev& m, unsigned long long key, int bit) {
   bool ins;
   const int slot = hash_insert(m, key, ins);
@@ -133,66 +76,228 @@ __device__ __forceinline__ void claim_block(const MapDev& m, unsigned long long 
       atomicOr(m.counters + kCntStatus, (unsigned long long)kStPoolFull);
     }
   }
-  const uint32_t b = 1u << bit;
-  if (__ldcg(m.mask + slot) & b) return;
-  if (atomicOr(m.mask + slot, b) == 0u) {
+  if (atomicOr(m.mask + slot, 1u << bit) == 0u) {
     const uint32_t idx = atomicAdd(m.ctl, 1u);
     if (idx < m.list_cap) m.list[idx] = (uint32_t)slot;
     else atomicOr(m.counters + kCntStatus, (unsigned long long)kStListFull);
   }
 }
 
-template <int NF, int NM>
+// Walk in anchor-relative cell coordinates with a 32-bit key
+// (cx + 512) | (cy + 512) << 10 | (cz + 512) << 20; used when the segment
+// starts within kRelStart cells of the anchor, so that every cell of the walk
+// (at most kMaxCells steps) stays inside the 10-bit fields.  Same decision
+// sequence as Walk.
+constexpr int kRelBias = 512;
+constexpr float kRelStart = 470.0f;
+constexpr uint32_t kEmptyRel = 0xFFFFFFFFu;
+
+struct Walk32 {
+  uint32_t key;
+  uint32_t kx, ky, kz;  // key change of one step along each axis
+  float bx, by, bz;     // next boundary per axis
+  float fx, fy, fz;     // step per axis (+1, -1, 0)
+  float ix, iy, iz;
+  float tx, ty, tz;
+  float ox, oy, oz;
+  float s1;
+  int n;
+
+  __device__ __forceinline__ void axis(float d, float fl, float o, uint32_t unit, float& f,
+                                       uint32_t& k, float& inv, float& b, float& t) {
+    const bool pos = d > 0.0f, neg = d < 0.0f;
+    f = pos ? 1.0f : (neg ? -1.0f : 0.0f);
+    k = pos ? unit : (neg ? 0u - unit : 0u);
+    inv = (pos || neg) ? __frcp_rn(d) : 0.0f;
+    b = pos ? fl + 1.0f : fl;
+    t = (pos || neg) ? __fmul_rn(__fsub_rn(b, o), inv) : __int_as_float(0x7f800000);
+  }
+  // start cell = floor(o + s0 dir); px, py, pz is that point.  The key
+  // counts cells from `base` (anchor-relative); only the key's origin
+  // depends on it, not the walk's arithmetic.
+  __device__ __forceinline__ void start(float px, float py, float pz, float ox_, float oy_, float oz_,
+                                        float dx, float dy, float dz, float s1_, int bx0, int by0,
+                                        int bz0, uint32_t flag) {
+    ox = ox_;
+    oy = oy_;
+    oz = oz_;
+    const float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
+    key = ((uint32_t)((int)flx - bx0 + kRelBias) | ((uint32_t)((int)fly - by0 + kRelBias) << 10) |
+           ((uint32_t)((int)flz - bz0 + kRelBias) << 20)) | flag;
+    axis(dx, flx, ox, 1u, fx, kx, ix, bx, tx);
+    axis(dy, fly, oy, 1u << 10, fy, ky, iy, by, ty);
+    axis(dz, flz, oz, 1u << 20, fz, kz, iz, bz, tz);
+    s1 = s1_;
+    n = 1;
+  }
+  __device__ __forceinline__ bool next() {
+    const bool sy_ = ty < tx;
+    const float t01 = sy_ ? ty : tx;
+    const bool sz_ = tz < t01;
+    const float t = sz_ ? tz : t01;
+    if (!(t <= s1) || n == kMaxCells) return false;
+    if (sz_) {
+      key += kz;
+      bz += fz;
+      tz = __fmul_rn(__fsub_rn(bz, oz), iz);
+    } else if (sy_) {
+      key += ky;
+      by += fy;
+      ty = __fmul_rn(__fsub_rn(by, oy), iy);
+    } else {
+      key += kx;
+      bx += fx;
+      tx = __fmul_rn(__fsub_rn(bx, ox), ix);
+    }
+    ++n;
+    return true;
+  }
+};
+
+__device__ __forceinline__ unsigned long long rel_to_key(uint32_t r, const int* a, int bx0 = 0,
+                                                         int by0 = 0, int bz0 = 0) {
+  return pack_key(a[0] + bx0 + (int)(r & 1023u) - kRelBias,
+                  a[1] + by0 + (int)((r >> 10) & 1023u) - kRelBias,
+                  a[2] + bz0 + (int)((r >> 20) & 1023u) - kRelBias);
+}
+constexpr uint32_t kFarFlag = 1u << 30;  // key counted from the segment's own start cell
+
+// CTA-local set of relative block keys (open addressing in shared memory).
+// Returns false when the key could not be placed within kSetProbes slots;
+// the caller then claims it globally itself.
+__device__ __forceinline__ bool set_insert(uint32_t* set, uint32_t key) {
+  uint32_t h = (key * 0x9E3779B1u) >> (32 - kSetBits);
+  volatile uint32_t* vs = set;
+#pragma unroll 1
+  for (int probe = 0; probe < kSetProbes; ++probe) {
+    const uint32_t cur = vs[h];
+    if (cur == key) return true;
+    if (cur == kEmptyRel) {
+      const uint32_t old = atomicCAS(set + h, kEmptyRel, key);
+      if (old == kEmptyRel || old == key) return true;
+    }
+    h = (h + 1) & (kSetSize - 1);
+  }
+  return false;
+}
+
+// Band segment of pixel (i, j) (Sec. IV-B ray through the block grid): ray
+// direction in anchor-relative block units per unit of depth (camera) or
+// range (LiDAR) and the band [max(d - tau, 0), d + tau].  False if the pixel
+// is outside the image or its depth is invalid.
+__device__ __forceinline__ bool pixel_segment(const FrameDev& F, const MapDev& m,
+                                              const float* s_ray, int i, int j, int lane, int ty,
+                                              float d, float& dx, float& dy, float& dz, float& s0,
+                                              float& s1) {
+  if (i >= F.width || j >= F.height) return false;
+  bool valid;
+  if (F.kind == kSensorPinhole) {
+    valid = d > 0.0f && d <= FLT_MAX;
+    const float rx = s_ray[lane], ry = s_ray[kTileW + ty];
+    dx = __fmaf_rn(F.M[0], rx, __fmaf_rn(F.M[1], ry, F.M[2]));
+    dy = __fmaf_rn(F.M[3], rx, __fmaf_rn(F.M[4], ry, F.M[5]));
+    dz = __fmaf_rn(F.M[6], rx, __fmaf_rn(F.M[7], ry, F.M[8]));
+  } else {
+    valid = d >= F.min_range && d <= F.max_range;
+    const float2 az = __ldg(reinterpret_cast<const float2*>(F.tab) + i);
+    const float2 el = __ldg(reinterpret_cast<const float2*>(F.tab) + F.width + j);
+    const float bx = __fmul_rn(el.y, az.x), by = __fmul_rn(el.y, az.y), bz = el.x;
+    dx = __fmaf_rn(F.M[0], bx, __fmaf_rn(F.M[1], by, __fmul_rn(F.M[2], bz)));
+    dy = __fmaf_rn(F.M[3], bx, __fmaf_rn(F.M[4], by, __fmul_rn(F.M[5], bz)));
+    dz = __fmaf_rn(F.M[6], bx, __fmaf_rn(F.M[7], by, __fmul_rn(F.M[8], bz)));
+  }
+  s0 = fmaxf(__fsub_rn(d, m.tau), 0.0f);
+  s1 = __fadd_rn(d, m.tau);
+  return valid;
+}
+
+// One CTA per kTileW x kTileH pixel tile of one frame.  Each warp walks the
+// band segments of one pixel row at a time; a lane whose left neighbour is
+// in the same block at the same step leaves that block to it, the others
+// record their block in a CTA-local set; then the tile's distinct blocks are
+// claimed in the global hash.  Segments that start far from the sensor's
+// block take a slower path with full keys and direct global claims.
+template <int NF, int NM, int TH>
 __global__ void __launch_bounds__(kAllocThreads)
     band_alloc_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
+  constexpr int kRows = TH * kTileW / kAllocThreads;  // pixel rows per thread
+  __shared__ uint32_t s_set[kSetSize];
+  __shared__ uint32_t s_keys[kSetSize];
+  __shared__ uint32_t s_nkeys;
+  __shared__ float s_ray[kTileW + TH];  // pinhole: (i - cu) / fu per column, (j - cv) / fv per row
+  for (int i = threadIdx.x; i < kSetSize; i += kAllocThreads) s_set[i] = kEmptyRel;
+  if (threadIdx.x == 0) s_nkeys = 0;
   int f = 0;
 #pragma unroll 1
   for (int k = 1; k < p.n_frames; ++k)
     if ((int)blockIdx.x >= p.fr[k].blk_begin) f = k;
   const FrameDev& F = p.fr[f];
   const MapDev& m = p.maps[F.map];
-  const int pix = ((int)blockIdx.x - F.blk_begin) * kAllocThreads + (int)threadIdx.x;
-  const int npix = F.width * F.height;
+  const int tiles_x = (F.width + kTileW - 1) / kTileW;
+  const int tile = (int)blockIdx.x - F.blk_begin;
+  const int x0 = (tile % tiles_x) * kTileW, y0 = (tile / tiles_x) * TH;
+  const int lane = threadIdx.x % kTileW, wy = threadIdx.x / kTileW;
+  // all of this thread's depths are requested before any is used
+  float dep[kRows];
+#pragma unroll
+  for (int q = 0; q < kRows; ++q) {
+    const int i = x0 + lane, j = y0 + wy + q * (kAllocThreads / kTileW);
+    dep[q] = (i < F.width && j < F.height) ? __ldg(F.depth + (size_t)j * F.width + i) : 0.0f;
+  }
+  if (F.kind == kSensorPinhole) {
+    if (threadIdx.x < kTileW)
+      s_ray[threadIdx.x] = __fdiv_rn(__fsub_rn((float)(x0 + (int)threadIdx.x), F.cu), F.fu);
+    else if (threadIdx.x < kTileW + TH)
+      s_ray[threadIdx.x] = __fdiv_rn(__fsub_rn((float)(y0 + (int)threadIdx.x - kTileW), F.cv), F.fv);
+  }
+  __syncthreads();
 
-  Walk wk;
-  bool live = false;
-  if (pix < npix) {
-    const float d = __ldg(F.depth + pix);
-    const int i = pix % F.width, j = pix / F.width;
-    float dx, dy, dz;
-    bool valid;
-    if (F.kind == kSensorPinhole) {
-      valid = d > 0.0f && d <= FLT_MAX;
-      const float rx = __fdiv_rn(__fsub_rn((float)i, F.cu), F.fu);
-      const float ry = __fdiv_rn(__fsub_rn((float)j, F.cv), F.fv);
-      dx = __fmaf_rn(F.M[0], rx, __fmaf_rn(F.M[1], ry, F.M[2]));
-      dy = __fmaf_rn(F.M[3], rx, __fmaf_rn(F.M[4], ry, F.M[5]));
-      dz = __fmaf_rn(F.M[6], rx, __fmaf_rn(F.M[7], ry, F.M[8]));
-    } else {
-      valid = d >= F.min_range && d <= F.max_range;
-      const float2 az = __ldg(reinterpret_cast<const float2*>(F.tab) + i);
-      const float2 el = __ldg(reinterpret_cast<const float2*>(F.tab) + F.width + j);
-      const float bx = __fmul_rn(el.y, az.x), by = __fmul_rn(el.y, az.y), bz = el.x;
-      dx = __fmaf_rn(F.M[0], bx, __fmaf_rn(F.M[1], by, __fmul_rn(F.M[2], bz)));
-      dy = __fmaf_rn(F.M[3], bx, __fmaf_rn(F.M[4], by, __fmul_rn(F.M[5], bz)));
-      dz = __fmaf_rn(F.M[6], bx, __fmaf_rn(F.M[7], by, __fmul_rn(F.M[8], bz)));
+#pragma unroll
+  for (int q = 0; q < kRows; ++q) {
+    const int ty = wy + q * (kAllocThreads / kTileW);
+    bool live = false;
+    Walk32 wk;
+    wk.key = kEmptyRel;
+    int b0x = 0, b0y = 0, b0z = 0;  // key origin of a far segment
+    float dx, dy, dz, s0, s1;
+    if (pixel_segment(F, m, s_ray, x0 + lane, y0 + ty, lane, ty, dep[q], dx, dy, dz, s0, s1)) {
+      const float px = __fmaf_rn(s0, dx, F.o[0]), py = __fmaf_rn(s0, dy, F.o[1]),
+                  pz = __fmaf_rn(s0, dz, F.o[2]);
+      if (fabsf(px) < kRelStart && fabsf(py) < kRelStart && fabsf(pz) < kRelStart) {
+        wk.start(px, py, pz, F.o[0], F.o[1], F.o[2], dx, dy, dz, s1, 0, 0, 0, 0u);
+        live = true;
+      } else if (fabsf(px) < 262144.0f && fabsf(py) < 262144.0f && fabsf(pz) < 262144.0f) {
+        // far from the sensor's block (long range or small voxels): count
+        // cells from the start cell and claim them globally one by one
+        b0x = (int)floorf(px);
+        b0y = (int)floorf(py);
+        b0z = (int)floorf(pz);
+        wk.start(px, py, pz, F.o[0], F.o[1], F.o[2], dx, dy, dz, s1, b0x, b0y, b0z, kFarFlag);
+        live = true;
+      }
     }
-    if (valid) {
-      const float s0 = fmaxf(__fsub_rn(d, m.tau), 0.0f), s1 = __fadd_rn(d, m.tau);
-      live = wk.start(F.o, dx, dy, dz, s0, s1);
-    }
-  }
-  const unsigned lane = threadIdx.x & 31u;
-  while (true) {
-    const unsigned act = __ballot_sync(0xffffffffu, live);
-    if (act == 0u) break;
-    if (live) {
-      const unsigned long long key = pack_key(F.a[0] + wk.cx, F.a[1] + wk.cy, F.a[2] + wk.cz);
-      const unsigned peers = __match_any_sync(act, key);
-      if (lane == (unsigned)(__ffs(peers) - 1)) claim_block(m, key, F.bit);
-      live = wk.next(F.o);
+    while (__any_sync(0xffffffffu, live)) {
+      const uint32_t left = __shfl_up_sync(0xffffffffu, wk.key, 1);
+      if (live) {
+        if (wk.key & kFarFlag) {
+          claim_block(m, rel_to_key(wk.key & ~kFarFlag, F.a, b0x, b0y, b0z), F.bit);
+        } else if (!(lane > 0 && left == wk.key) && !set_insert(s_set, wk.key)) {
+          claim_block(m, rel_to_key(wk.key, F.a), F.bit);
+        }
+        live = wk.next();
+        if (!live) wk.key = kEmptyRel;
+      }
     }
   }
+  __syncthreads();
+  // compact the tile's distinct blocks, then claim them one per thread
+  for (int i = threadIdx.x; i < kSetSize; i += kAllocThreads) {
+    const uint32_t key = s_set[i];
+    if (key != kEmptyRel) s_keys[atomicAdd(&s_nkeys, 1u)] = key;
+  }
+  __syncthreads();
+  const uint32_t nk = s_nkeys;
+  for (uint32_t i = threadIdx.x; i < nk; i += kAllocThreads) claim_block(m, rel_to_key(s_keys[i], F.a), F.bit);
 }
 
 // ------------------------------------------------ per-voxel projection
@@ -332,15 +437,94 @@ struct Voxels4<kStorageF16> {
   }
 };
 
+// A thread's four voxels: block (bx, by, bz), local x = lx0 .. lx0 + 3 at
+// local (ly, lz).
+struct VoxelRow {
+  int bx, by, bz, lx0, ly, lz;
+};
+
+// Voxel centres of a row in frame F's sensor frame (Eq. 1), in the FP32
+// decision sequence p_i = fma(R_i0, qx, fma(R_i1, qy, fma(R_i2, qz, t_i))).
+__device__ __forceinline__ void row_points(const FrameDev& F, float v, const VoxelRow& r,
+                                           float* px, float* py, float* pz) {
+  const int rx = (r.bx - F.a[0]) * 8 + r.lx0;
+  const int ry = (r.by - F.a[1]) * 8 + r.ly;
+  const int rz = (r.bz - F.a[2]) * 8 + r.lz;
+  const float qy = __fmul_rn(__fadd_rn((float)ry, 0.5f), v);
+  const float qz = __fmul_rn(__fadd_rn((float)rz, 0.5f), v);
+  const float cx = __fmaf_rn(F.Rcl[1], qy, __fmaf_rn(F.Rcl[2], qz, F.tloc[0]));
+  const float cy = __fmaf_rn(F.Rcl[4], qy, __fmaf_rn(F.Rcl[5], qz, F.tloc[1]));
+  const float cz = __fmaf_rn(F.Rcl[7], qy, __fmaf_rn(F.Rcl[8], qz, F.tloc[2]));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float qx = __fmul_rn(__fadd_rn((float)(rx + i), 0.5f), v);
+    px[i] = __fmaf_rn(F.Rcl[0], qx, cx);
+    py[i] = __fmaf_rn(F.Rcl[3], qx, cy);
+    pz[i] = __fmaf_rn(F.Rcl[6], qx, cz);
+  }
+}
+
+// NQ consecutive pinhole frames of the batch: phase 1 projects every voxel
+// into every frame (Eq. 2, nearest pixel) and issues all depth loads, phase 2
+// applies the updates in frame order.  An out-of-image projection reads no
+// pixel and yields d = 0, which is invalid like a missing depth.
+template <int NQ, class P>
+__device__ __forceinline__ void fuse_pinhole(const P& p, const int (&fq)[4], const MapDev& m,
+                                             const VoxelRow& r, float* D, float* W,
+                                             unsigned long long& upd) {
+  float d[NQ][4], z[NQ][4];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const FrameDev& F = p.fr[fq[q]];
+    float px[4], py[4];
+    row_points(F, m.v, r, px, py, z[q]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float iz = __frcp_rn(z[q][i]);
+      const float u = __fadd_rn(__fmaf_rn(__fmul_rn(px[i], iz), F.fu, F.cu), 0.5f);
+      const float v = __fadd_rn(__fmaf_rn(__fmul_rn(py[i], iz), F.fv, F.cv), 0.5f);
+      const bool in = z[q][i] > 0.0f && u >= 0.0f && u < (float)F.width && v >= 0.0f &&
+                      v < (float)F.height;
+      d[q][i] = in ? __ldg(F.depth + (int)v * F.width + (int)u) : 0.0f;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float dp = __fsub_rn(d[q][i], z[q][i]);
+      if (d[q][i] > 0.0f && d[q][i] <= FLT_MAX && !(dp < -m.tau)) {
+        fuse(D[i], W[i], fminf(dp, m.tau), m.wmax);
+        ++upd;
+      }
+    }
+}
+
+// One frame of any sensor kind, voxel by voxel.
+__device__ __forceinline__ void fuse_any(const FrameDev& F, const MapDev& m, const VoxelRow& r,
+                                         float* D, float* W, unsigned long long& upd) {
+  float px[4], py[4], pz[4];
+  row_points(F, m.v, r, px, py, pz);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float d, dv;
+    if (!sample(F, m, px[i], py[i], pz[i], d, dv)) continue;
+    const float dp = __fsub_rn(d, dv);
+    if (dp < -m.tau) continue;
+    fuse(D[i], W[i], fminf(dp, m.tau), m.wmax);
+    ++upd;
+  }
+}
+
 template <int NF, int NM, int STORAGE>
 __global__ void __launch_bounds__(kIntegrateThreads)
     integrate_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
   __shared__ uint32_t s_begin[NM + 1];
-  __shared__ uint32_t s_map, s_slot, s_mask;
-  __shared__ int32_t s_val;
-  __shared__ unsigned long long s_key;
-  __shared__ unsigned long long s_upd[kIntegrateThreads / 32];
+  __shared__ unsigned long long s_upd[NM];
+  __shared__ uint32_t s_next[2];
   const int t = threadIdx.x;
+  if (t < NM) s_upd[t] = 0ull;
+  if (t == 0) s_next[0] = blockIdx.x;
   if (t == 0) {
     // the batch's work = the concatenation of every map's list
     uint32_t acc = 0;
@@ -355,21 +539,21 @@ __global__ void __launch_bounds__(kIntegrateThreads)
   // this thread's voxels: x = lx0 .. lx0 + 3 at (ly, lz)
   const int lx0 = (t & 1) * 4, ly = (t >> 1) & 7, lz = t >> 4;
 
-  for (uint32_t e = blockIdx.x; e < n; e += gridDim.x) {
-    if (t == 0) {
-      int mi = 0;
-      while (mi + 1 < p.n_maps && e >= s_begin[mi + 1]) ++mi;
-      const MapDev& m0 = p.maps[mi];
-      const uint32_t slot = m0.list[e - s_begin[mi]];
-      s_map = mi;
-      s_slot = slot;
-      s_val = m0.vals[slot];
-      s_mask = m0.mask[slot];
-      s_key = m0.keys[slot];
-    }
-    __syncthreads();
-    const MapDev& m = p.maps[s_map];
-    const int val = s_val;
+  // entries are handed out dynamically (blocks differ in their frame
+  // counts); s_next is double-buffered so one barrier per entry suffices
+  for (uint32_t it = 0;; ++it) {
+    const uint32_t e = s_next[it & 1u];
+    if (e >= n) break;
+    if (t == 0) s_next[(it + 1) & 1u] = gridDim.x + atomicAdd(p.maps[0].ctl + 2, 1u);
+    // every thread reads the entry's metadata itself (same addresses across
+    // the CTA), so no warp waits on another before its voxel loads
+    int mi = 0;
+    while (mi + 1 < p.n_maps && e >= s_begin[mi + 1]) ++mi;
+    const MapDev& m = p.maps[mi];
+    const uint32_t slot = m.list[e - s_begin[mi]];
+    const int val = m.vals[slot];
+    const uint32_t slot_mask = m.mask[slot];
+    const unsigned long long slot_key = m.keys[slot];
     const bool fresh = val <= -2;
     const int pool = fresh ? -val - 2 : val;
     unsigned long long my_upd = 0;
@@ -381,57 +565,65 @@ __global__ void __launch_bounds__(kIntegrateThreads)
       } else {
         Voxels4<STORAGE>::load(m, pool, t, D, W);
       }
-      const int bx = key_coord(s_key, 0), by = key_coord(s_key, 1), bz = key_coord(s_key, 2);
-      uint32_t bits = s_mask;
+      const int bx = key_coord(slot_key, 0), by = key_coord(slot_key, 1), bz = key_coord(slot_key, 2);
+      const VoxelRow vr{bx, by, bz, lx0, ly, lz};
+      uint32_t bits = slot_mask;
       while (bits) {
-        // bit k of the mask is frame k of the batch; frames apply in batch order
-        const int f = __ffs(bits) - 1;
-        bits &= bits - 1u;
-        const FrameDev& F = p.fr[f];
-        const int rx = (bx - F.a[0]) * 8 + lx0;
-        const int ry = (by - F.a[1]) * 8 + ly;
-        const int rz = (bz - F.a[2]) * 8 + lz;
-        const float qy = __fmul_rn(__fadd_rn((float)ry, 0.5f), m.v);
-        const float qz = __fmul_rn(__fadd_rn((float)rz, 0.5f), m.v);
-        // innermost terms of p_i = fma(R_i0, qx, fma(R_i1, qy, fma(R_i2, qz, t_i)))
-        const float cx = __fmaf_rn(F.Rcl[1], qy, __fmaf_rn(F.Rcl[2], qz, F.tloc[0]));
-        const float cy = __fmaf_rn(F.Rcl[4], qy, __fmaf_rn(F.Rcl[5], qz, F.tloc[1]));
-        const float cz = __fmaf_rn(F.Rcl[7], qy, __fmaf_rn(F.Rcl[8], qz, F.tloc[2]));
+        // bit k of the mask is frame k of the batch; frames apply in batch
+        // order.  Runs of up to four pinhole frames issue all their depth
+        // loads before the first update.
+        int fq[4];
+        int nq = 0;
+        bool go = true;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float qx = __fmul_rn(__fadd_rn((float)(rx + i), 0.5f), m.v);
-          const float px = __fmaf_rn(F.Rcl[0], qx, cx);
-          const float py = __fmaf_rn(F.Rcl[3], qx, cy);
-          const float pz = __fmaf_rn(F.Rcl[6], qx, cz);
-          float d, dv;
-          if (!sample(F, m, px, py, pz, d, dv)) continue;
-          const float dp = __fsub_rn(d, dv);
-          if (dp < -m.tau) continue;
-          fuse(D[i], W[i], fminf(dp, m.tau), m.wmax);
-          ++my_upd;
+        for (int q = 0; q < 4; ++q) {
+          fq[q] = -1;
+          if (go && bits) {
+            const int f = __ffs(bits) - 1;
+            if (p.fr[f].kind == kSensorPinhole) {
+              fq[q] = f;
+              ++nq;
+              bits &= bits - 1u;
+            } else {
+              go = false;
+            }
+          }
+        }
+        if (nq == 4) fuse_pinhole<4>(p, fq, m, vr, D, W, my_upd);
+        else if (nq == 3) fuse_pinhole<3>(p, fq, m, vr, D, W, my_upd);
+        else if (nq == 2) fuse_pinhole<2>(p, fq, m, vr, D, W, my_upd);
+        else if (nq == 1) fuse_pinhole<1>(p, fq, m, vr, D, W, my_upd);
+        else {
+          const int f = __ffs(bits) - 1;  // a LiDAR frame
+          bits &= bits - 1u;
+          fuse_any(p.fr[f], m, vr, D, W, my_upd);
         }
       }
       Voxels4<STORAGE>::store(m, pool, t, D, W);
     }
-    // per-map update count: warp sums, one atomic per CTA and block
+    // per-map update count: warp sums into a shared per-map counter
     for (int o = 16; o > 0; o >>= 1) my_upd += __shfl_down_sync(0xffffffffu, my_upd, o);
-    if ((t & 31) == 0) s_upd[t >> 5] = my_upd;
-    __syncthreads();
+    if ((t & 31) == 0 && my_upd) atomicAdd(&s_upd[mi], my_upd);
+    __syncthreads();  // every warp has read this entry's metadata
     if (t == 0) {
-      unsigned long long tot = 0;
-      for (int k = 0; k < kIntegrateThreads / 32; ++k) tot += s_upd[k];
-      if (tot) atomicAdd(m.counters + kCntUpdates, tot);
-      m.mask[s_slot] = 0u;
-      if (fresh) m.vals[s_slot] = pool;
+      m.mask[slot] = 0u;
+      if (fresh) m.vals[slot] = pool;
     }
   }
+  __syncthreads();
+  if (t < p.n_maps && s_upd[t]) atomicAdd(p.maps[t].counters + kCntUpdates, s_upd[t]);
   // the last CTA to finish resets every map's work list for the next batch
   if (t == 0) {
     __threadfence();
     const unsigned done = atomicAdd(p.maps[0].ctl + 1, 1u);
     if (done == gridDim.x - 1) {
-      for (int k = 0; k < p.n_maps; ++k) p.maps[k].ctl[0] = 0u;
+      for (int k = 0; k < p.n_maps; ++k) {
+        atomicAdd(p.maps[k].counters + kCntVisits, (unsigned long long)(s_begin[k + 1] - s_begin[k]));
+        atomicAdd(p.maps[k].counters + kCntLaunches, 1ull);
+        p.maps[k].ctl[0] = 0u;
+      }
       p.maps[0].ctl[1] = 0u;
+      p.maps[0].ctl[2] = 0u;
     }
   }
 }
@@ -475,15 +667,18 @@ __global__ void reset_kernel(const MapDev m, uint32_t cap) {
     m.mask[i] = 0u;
   }
   if (blockIdx.x == 0 && threadIdx.x < kNumCounters) m.counters[threadIdx.x] = 0ull;
-  if (blockIdx.x == 0 && threadIdx.x < 2) m.ctl[threadIdx.x] = 0u;
+  if (blockIdx.x == 0 && threadIdx.x < 4) m.ctl[threadIdx.x] = 0u;
 }
 
 }  // namespace
 
 template <int NF, int NM>
-cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, cudaStream_t s) {
+cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile_h, cudaStream_t s) {
   if (n_ctas <= 0) return cudaSuccess;
-  band_alloc_kernel<NF, NM><<<n_ctas, kAllocThreads, 0, s>>>(p);
+  if (tile_h == kTileHBig)
+    band_alloc_kernel<NF, NM, kTileHBig><<<n_ctas, kAllocThreads, 0, s>>>(p);
+  else
+    band_alloc_kernel<NF, NM, kTileHSmall><<<n_ctas, kAllocThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -497,9 +692,9 @@ cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStrea
   return cudaGetLastError();
 }
 
-template cudaError_t launch_band_alloc<1, 1>(const BatchParams<1, 1>&, int, cudaStream_t);
+template cudaError_t launch_band_alloc<1, 1>(const BatchParams<1, 1>&, int, int, cudaStream_t);
 template cudaError_t launch_band_alloc<kMaxFrames, kMaxMaps>(const BatchParams<kMaxFrames, kMaxMaps>&,
-                                                             int, cudaStream_t);
+                                                             int, int, cudaStream_t);
 template cudaError_t launch_integrate<1, 1>(const BatchParams<1, 1>&, int, cudaStream_t);
 template cudaError_t launch_integrate<kMaxFrames, kMaxMaps>(const BatchParams<kMaxFrames, kMaxMaps>&,
                                                             int, cudaStream_t);

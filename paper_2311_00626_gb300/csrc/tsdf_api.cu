@@ -37,11 +37,16 @@ struct tsdf_map {
   int64_t frames;
   unsigned long long status_seen;  // device status bits observed by the host
   std::vector<LidarTable> tables;
+  // diagnostics: event triples (before alloc, between, after integrate)
+  bool timing;
+  std::vector<cudaEvent_t> events;
+  size_t n_timed;
 };
 
 namespace {
 
 constexpr int64_t kDefaultBlocks = 1 << 18;
+constexpr size_t kTimedCalls = 4096;
 
 tsdf_status cuda_fail() {
   cudaGetLastError();
@@ -176,13 +181,23 @@ tsdf_status fill_frame(tsdf_map* m, int map_index, int kind, const tsdf_pinhole*
   return TSDF_OK;
 }
 
-int alloc_ctas(const FrameDev& F) {
-  return (F.width * F.height + gbt::kAllocThreads - 1) / gbt::kAllocThreads;
+int alloc_ctas(const FrameDev& F, int tile_h) {
+  return ((F.width + gbt::kTileW - 1) / gbt::kTileW) * ((F.height + tile_h - 1) / tile_h);
+}
+
+int pick_tile_h(int64_t pixels) {
+  return pixels >= gbt::kBigTilePixels ? gbt::kTileHBig : gbt::kTileHSmall;
 }
 
 bool on_device(const tsdf_map* m) {
   int dev = -1;
   return cudaGetDevice(&dev) == cudaSuccess && dev == m->device;
+}
+
+// Next free event triple when timing is enabled, else nullptr.
+cudaEvent_t* timing_slot(tsdf_map* m) {
+  if (!m->timing || m->n_timed >= kTimedCalls) return nullptr;
+  return &m->events[3 * m->n_timed++];
 }
 
 tsdf_status integrate_one(tsdf_map* m, int kind, const tsdf_pinhole* ph, const tsdf_lidar* li,
@@ -200,8 +215,13 @@ tsdf_status integrate_one(tsdf_map* m, int kind, const tsdf_pinhole* ph, const t
   p.fr[0].blk_begin = 0;
   p.fr[0].bit = 0;
   cudaStream_t s = (cudaStream_t)stream;
-  if (gbt::launch_band_alloc(p, alloc_ctas(p.fr[0]), s) != cudaSuccess) return cuda_fail();
+  cudaEvent_t* ev = timing_slot(m);
+  if (ev) cudaEventRecord(ev[0], s);
+  const int th = pick_tile_h((int64_t)p.fr[0].width * p.fr[0].height);
+  if (gbt::launch_band_alloc(p, alloc_ctas(p.fr[0], th), th, s) != cudaSuccess) return cuda_fail();
+  if (ev) cudaEventRecord(ev[1], s);
   if (gbt::launch_integrate(p, m->n_ctas_integrate, s) != cudaSuccess) return cuda_fail();
+  if (ev) cudaEventRecord(ev[2], s);
   m->frames += 1;
   return TSDF_OK;
 }
@@ -225,6 +245,7 @@ void free_map(tsdf_map* m) {
   cudaFree(m->dev.list);
   cudaFree(m->dev.ctl);
   for (LidarTable& t : m->tables) cudaFree(t.dev);
+  for (cudaEvent_t e : m->events) cudaEventDestroy(e);
   delete m;
 }
 
@@ -262,6 +283,8 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   m->Bd = 8.0 * m->vd;
   m->frames = 0;
   m->status_seen = 0;
+  m->timing = false;
+  m->n_timed = 0;
   MapDev& d = m->dev;
   d.cap_mask = (uint32_t)(cap - 1);
   d.max_blocks = (int32_t)o.max_blocks;
@@ -281,7 +304,7 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
             cudaMalloc(&d.block_keys, sizeof(unsigned long long) * o.max_blocks) == cudaSuccess &&
             cudaMalloc(&d.counters, sizeof(unsigned long long) * gbt::kNumCounters) == cudaSuccess &&
             cudaMalloc(&d.list, sizeof(uint32_t) * o.max_blocks) == cudaSuccess &&
-            cudaMalloc(&d.ctl, sizeof(unsigned int) * 2) == cudaSuccess;
+            cudaMalloc(&d.ctl, sizeof(unsigned int) * 4) == cudaSuccess;
   if (ok) ok = gbt::launch_reset(d, m->cap, 0) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
   if (!ok) {
     free_map(m);
@@ -331,19 +354,28 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
     p.maps[i] = maps[i]->dev;
     integ = std::max(integ, maps[i]->n_ctas_integrate);
   }
+  int64_t pixels = 0;
   for (int f = 0; f < n; ++f) {
     const tsdf_frame_desc& fd = frames[f];
     if (fd.map < 0 || fd.map >= n_maps) return TSDF_ERR_ARG;
     tsdf_status st = fill_frame(maps[fd.map], fd.map, fd.kind, &fd.pinhole, &fd.lidar,
                                 fd.depth_dev, fd.T_world_sensor, p.fr[f]);
     if (st != TSDF_OK) return st;
-    p.fr[f].blk_begin = ctas;
     p.fr[f].bit = f;
-    ctas += alloc_ctas(p.fr[f]);
+    pixels += (int64_t)p.fr[f].width * p.fr[f].height;
+  }
+  const int th = pick_tile_h(pixels);
+  for (int f = 0; f < n; ++f) {
+    p.fr[f].blk_begin = ctas;
+    ctas += alloc_ctas(p.fr[f], th);
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  if (gbt::launch_band_alloc(p, ctas, s) != cudaSuccess) return cuda_fail();
+  cudaEvent_t* ev = timing_slot(maps[0]);
+  if (ev) cudaEventRecord(ev[0], s);
+  if (gbt::launch_band_alloc(p, ctas, th, s) != cudaSuccess) return cuda_fail();
+  if (ev) cudaEventRecord(ev[1], s);
   if (gbt::launch_integrate(p, integ, s) != cudaSuccess) return cuda_fail();
+  if (ev) cudaEventRecord(ev[2], s);
   for (int f = 0; f < n; ++f) maps[frames[f].map]->frames += 1;
   return TSDF_OK;
 }
@@ -375,7 +407,7 @@ tsdf_status map_num_blocks(const tsdf_map* map, int64_t* out) {
   return TSDF_OK;
 }
 
-tsdf_status map_stats(const tsdf_map* map, int64_t out[4]) {
+tsdf_status map_stats(const tsdf_map* map, int64_t out[6]) {
   if (!map || !out) return TSDF_ERR_ARG;
   unsigned long long c[gbt::kNumCounters];
   tsdf_status st = read_counters(map, c);
@@ -384,6 +416,37 @@ tsdf_status map_stats(const tsdf_map* map, int64_t out[4]) {
   out[1] = (int64_t)c[gbt::kCntUpdates];
   out[2] = map->frames;
   out[3] = (int64_t)map->status_seen;
+  out[4] = (int64_t)c[gbt::kCntVisits];
+  out[5] = (int64_t)c[gbt::kCntLaunches];
+  return TSDF_OK;
+}
+
+tsdf_status map_timing(tsdf_map* map, int32_t enable) {
+  if (!map) return TSDF_ERR_ARG;
+  if (enable && map->events.empty()) {
+    map->events.resize(3 * kTimedCalls);
+    for (cudaEvent_t& e : map->events)
+      if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail();
+  }
+  map->timing = enable != 0;
+  map->n_timed = 0;
+  return TSDF_OK;
+}
+
+tsdf_status map_kernel_times(tsdf_map* map, double out_ms[2], int64_t* calls) {
+  if (!map || !out_ms || !calls) return TSDF_ERR_ARG;
+  out_ms[0] = out_ms[1] = 0.0;
+  for (size_t i = 0; i < map->n_timed; ++i) {
+    cudaEvent_t* e = &map->events[3 * i];
+    float a = 0.0f, b = 0.0f;
+    if (cudaEventSynchronize(e[2]) != cudaSuccess || cudaEventElapsedTime(&a, e[0], e[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&b, e[1], e[2]) != cudaSuccess)
+      return cuda_fail();
+    out_ms[0] += a;
+    out_ms[1] += b;
+  }
+  *calls = (int64_t)map->n_timed;
+  map->n_timed = 0;
   return TSDF_OK;
 }
 

@@ -15,11 +15,25 @@ constexpr int kMaxCells = 32;          // cap on blocks met by one band segment
 constexpr int kMaxFrames = 32;         // frames per batch (one bit each in the slot mask)
 constexpr int kMaxMaps = 16;           // maps per batch
 constexpr unsigned long long kEmptyKey = ~0ull;
-constexpr int kAllocThreads = 256;     // pixels per allocation CTA
+constexpr int kAllocThreads = 256;     // threads per allocation CTA
+constexpr int kTileW = 32;             // allocation CTA = one 32 x (16 or 32) pixel tile
+constexpr int kTileHSmall = 16;        // small launches: more CTAs
+constexpr int kTileHBig = 32;          // large launches: fewer, fuller CTAs
+constexpr int kBigTilePixels = 1 << 21;  // pixels per launch from which big tiles are used
+constexpr int kSetBits = 10;           // CTA-local block-key set: 1024 slots
+constexpr int kSetSize = 1 << kSetBits;
+constexpr int kSetProbes = 32;
 constexpr int kIntegrateThreads = 128; // 4 voxels per thread
 
 // Per-map u64 counters.
-enum : int { kCntBlocks = 0, kCntUpdates = 1, kCntStatus = 2, kNumCounters = 4 };
+enum : int {
+  kCntBlocks = 0,   // pool blocks handed out (may exceed max_blocks when full)
+  kCntUpdates = 1,  // voxel updates
+  kCntStatus = 2,   // sticky status bits
+  kCntVisits = 3,   // work-list entries consumed by integration launches
+  kCntLaunches = 4, // integration launches
+  kNumCounters = 6
+};
 // Sticky status bits.
 enum : unsigned long long { kStPoolFull = 1, kStHashFull = 2, kStListFull = 4, kStTimeout = 8 };
 
@@ -39,7 +53,8 @@ struct MapDev {
   unsigned long long* block_keys; // [max_blocks] key of each pool block
   unsigned long long* counters;   // [kNumCounters]
   uint32_t* list;                 // [list_cap] slots met by the current batch
-  unsigned int* ctl;              // [0] list length, [1] finished integration CTAs
+  unsigned int* ctl;              // [0] list length, [1] finished integration CTAs,
+                                  // [2] entries handed out (first map of a batch)
   uint32_t list_cap;
   uint32_t cap_mask;              // hash capacity - 1 (power of two)
   int32_t max_blocks;
@@ -77,14 +92,17 @@ struct BatchParams {
   FrameDev fr[NF];
 };
 
-// Block key: three 21-bit two's-complement coordinates, x lowest.
+// Block key: three 21-bit fields holding coordinate + 2^20 (x lowest), so a
+// unit step along an axis is a plain add of 1 << (21 * axis) to the key.
+// Bit 63 is always 0, so no key equals kEmptyKey.
+constexpr int kKeyBias = 1 << 20;
 __host__ __device__ __forceinline__ unsigned long long pack_key(int x, int y, int z) {
-  return ((unsigned long long)(x & 0x1FFFFF)) | ((unsigned long long)(y & 0x1FFFFF) << 21) |
-         ((unsigned long long)(z & 0x1FFFFF) << 42);
+  return (unsigned long long)(unsigned)(x + kKeyBias) |
+         ((unsigned long long)(unsigned)(y + kKeyBias) << 21) |
+         ((unsigned long long)(unsigned)(z + kKeyBias) << 42);
 }
 __host__ __device__ __forceinline__ int key_coord(unsigned long long k, int axis) {
-  const int c = (int)((k >> (21 * axis)) & 0x1FFFFF);
-  return c >= (1 << 20) ? c - (1 << 21) : c;  // sign-extend 21 bits
+  return (int)((k >> (21 * axis)) & 0x1FFFFF) - kKeyBias;
 }
 // 64-bit finaliser (MurmurHash3 fmix64) for slot selection.
 __host__ __device__ __forceinline__ uint32_t hash_key(unsigned long long k) {
@@ -98,7 +116,7 @@ __host__ __device__ __forceinline__ uint32_t hash_key(unsigned long long k) {
 
 // Launchers (kernels.cu).
 template <int NF, int NM>
-cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, cudaStream_t s);
+cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile_h, cudaStream_t s);
 template <int NF, int NM>
 cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStream_t s);
 cudaError_t launch_query(const MapDev& m, const float* pts, int64_t n, float* dist, float* weight,

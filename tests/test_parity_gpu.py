@@ -304,3 +304,15 @@ def test_rig_mixed_sensors_batched():
         np.testing.assert_array_equal(a, b)
     orc, _ = run_oracle(w.frames, w.voxel_size)
     _record("rig2", compare(bat, orc, tol_lidar(w.voxel_size, 30.0), "rig2"))
+
+
+def test_far_segments_small_voxels():
+    """Half-millimetre voxels: band segments start about 500 blocks from the
+    sensor's block, beyond the allocator's short-key range, and take its
+    full-key path.  At this voxel size 1e-4 voxels (5e-8 m) is finer than the
+    FP32 spacing of a 2 m depth (2.4e-7 m), so the bound adds 2 ulp of the
+    largest depth."""
+    w = synth.config_tiny()
+    tol = tol_pinhole(0.0005) + 2 * float(np.spacing(np.float32(2.0)))
+    st = _parity("far_small_voxels", w.frames, 0.0005, tol)
+    assert st["blocks"] > 1000
