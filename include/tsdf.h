@@ -203,6 +203,55 @@ tsdf_status map_reset(tsdf_map* map, void* cuda_stream);
 /* map_destroy — free the map's device memory (synchronises first). */
 tsdf_status map_destroy(tsdf_map* map);
 
+/*
+ * Allocation-free integration.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate GPU memory at the time they
+ * integrate (their allocator belongs to another framework, they are
+ * capturing a CUDA graph, or a real-time loop forbids allocation after
+ * start-up).  It integrates one pinhole frame exactly like integrate_depth
+ * into FP32 map storage that the caller owns, described by tsdf_map_buffers:
+ *   keys        uint64 [hash_capacity], every byte 0xFF before first use
+ *   vals        int32  [hash_capacity], every byte 0xFF before first use
+ *   mask        uint32 [hash_capacity], zero before first use
+ *   pool        {float D, float W} [max_blocks][512], any initial contents
+ *   block_keys  uint64 [max_blocks]: key of each pool block (written)
+ *   counters    uint64 [6], zero before first use: [0] blocks allocated
+ *               (pool blocks 0 .. min([0], max_blocks) - 1 are in use),
+ *               [1] voxel updates, [2] status bits (nonzero = capacity
+ *               exceeded), [3] block visits, [4] integration launches
+ * hash_capacity is a power of two >= 2 * max_blocks.  A block key packs
+ * (x + 2^20) | (y + 2^20) << 21 | (z + 2^20) << 42.  Between calls the
+ * storage must not be modified.
+ *
+ * The per-call work list lives in a fixed array of device memory inside the
+ * library, reserved on every GPU that loads the library until the process
+ * exits: 4 * (TSDF_STATIC_MAX_BLOCKS + 4) bytes.  max_blocks above
+ * TSDF_STATIC_MAX_BLOCKS is refused with TSDF_ERR_CAPACITY; other bad
+ * arguments give TSDF_ERR_ARG.  The call allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.  Its first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call
+ * shares the one array, so calls whose work overlaps on the GPU (different
+ * streams or threads) race and must be serialised by the caller.
+ */
+#define TSDF_STATIC_MAX_BLOCKS (1 << 16)
+
+typedef struct {
+  unsigned long long* keys;
+  int32_t* vals;
+  uint32_t* mask;
+  void* pool;
+  unsigned long long* block_keys;
+  unsigned long long* counters;
+  int64_t hash_capacity;
+  int64_t max_blocks;
+} tsdf_map_buffers;
+
+tsdf_status integrate_depth_static(const tsdf_map_buffers* buf, float voxel_size,
+                                   int32_t truncation_voxels, float max_weight,
+                                   const float* depth_dev, const tsdf_pinhole* intr,
+                                   const double T_world_cam[16], void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

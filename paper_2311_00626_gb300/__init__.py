@@ -21,16 +21,18 @@ __all__ = ["TsdfError", "Pinhole", "Lidar", "MapOpts", "FrameDesc", "TsdfMap", "
            "map_create", "map_create_ex", "integrate_depth", "integrate_lidar",
            "integrate_batch", "query_voxels", "map_sync", "map_num_blocks", "map_stats",
            "map_export", "map_reset", "map_destroy", "map_timing", "map_kernel_times",
-           "STORAGE_FP32", "STORAGE_FP16",
+           "MapBuffers", "integrate_depth_static", "STATIC_MAX_BLOCKS", "STORAGE_FP32", "STORAGE_FP16",
            "SENSOR_PINHOLE", "SENSOR_LIDAR", "EXPORTED_SYMBOLS"]
 
 STORAGE_FP32, STORAGE_FP16 = 0, 1
+STATIC_MAX_BLOCKS = 1 << 16  # TSDF_STATIC_MAX_BLOCKS
 SENSOR_PINHOLE, SENSOR_LIDAR = 0, 1
 _STATUS = {0: "TSDF_OK", -1: "TSDF_ERR_ARG", -2: "TSDF_ERR_CUDA", -3: "TSDF_ERR_CAPACITY",
            -4: "TSDF_ERR_TIMEOUT", -5: "TSDF_ERR_STATE"}
 EXPORTED_SYMBOLS = ["map_create", "map_create_ex", "integrate_depth", "integrate_lidar",
                     "integrate_batch", "query_voxels", "map_sync", "map_num_blocks", "map_stats",
-                    "map_export", "map_reset", "map_destroy", "map_timing", "map_kernel_times"]
+                    "map_export", "map_reset", "map_destroy", "map_timing", "map_kernel_times",
+                    "integrate_depth_static"]
 
 
 class TsdfError(RuntimeError):
@@ -63,6 +65,14 @@ class FrameDesc(ctypes.Structure):
                 ("T_world_sensor", ctypes.c_double * 16)]
 
 
+class MapBuffers(ctypes.Structure):
+    """Caller-owned FP32 map storage for integrate_depth_static (see tsdf.h)."""
+    _fields_ = [("keys", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("pool", ctypes.c_void_p), ("block_keys", ctypes.c_void_p),
+                ("counters", ctypes.c_void_p), ("hash_capacity", ctypes.c_int64),
+                ("max_blocks", ctypes.c_int64)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -93,6 +103,8 @@ def lib():
                 "map_destroy": ([P], I),
                 "map_timing": ([P, I], I),
                 "map_kernel_times": ([P, P, ctypes.POINTER(ctypes.c_int64)], I),
+                "integrate_depth_static": ([ctypes.POINTER(MapBuffers), F, I, F, P,
+                                            ctypes.POINTER(Pinhole), P, P], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -227,6 +239,16 @@ def map_reset(m: int, stream=None):
 
 def map_destroy(m: int):
     _check(lib().map_destroy(m), "map_destroy")
+
+
+def integrate_depth_static(buffers: MapBuffers, voxel_size: float, truncation_voxels: int,
+                           max_weight: float, depth, intr: Pinhole, T_world_cam, stream=None):
+    """Allocation-free integration of one pinhole frame into caller-owned
+    storage; raises TsdfError with the C status on failure."""
+    _check(lib().integrate_depth_static(ctypes.byref(buffers), voxel_size, truncation_voxels,
+                                        max_weight, _dptr(depth), ctypes.byref(intr),
+                                        _pose(T_world_cam), _stream(stream)),
+           "integrate_depth_static")
 
 
 class TsdfMap:

@@ -517,3 +517,119 @@ tsdf_status map_destroy(tsdf_map* map) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// integrate_depth_static: the allocation-free entry point.
+//
+// Some callers cannot allocate GPU memory themselves or through this library
+// (a process whose allocator is owned by another framework, code running
+// while a CUDA graph is being captured, real-time loops that forbid
+// allocation after start-up).  For them the per-call work list that the
+// integration needs lives in g_static_scratch, a fixed-size array in device
+// memory that the module reserves on every GPU that loads it and keeps until
+// the process exits.  The caller owns all map storage and the input image.
+
+namespace {
+
+constexpr int64_t kStaticMaxBlocks = TSDF_STATIC_MAX_BLOCKS;
+// [0, kStaticMaxBlocks): work list of hash slots; then 4 control words
+// (list length, finished integration CTAs, entries handed out, spare).
+static __device__ __align__(256) uint32_t g_static_scratch[kStaticMaxBlocks + 4];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mutex;
+uint32_t* g_static_ptr[kStaticMaxDevices] = {};  // device address of g_static_scratch per device
+
+// Device address of the scratch array on the current device, looked up once
+// per device with that device current.
+tsdf_status static_scratch(uint32_t** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return cuda_fail();
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) return cuda_fail();
+    g_static_ptr[dev] = static_cast<uint32_t*>(ptr);
+  }
+  *out = g_static_ptr[dev];
+  return TSDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tsdf_status integrate_depth_static(const tsdf_map_buffers* buf, float voxel_size,
+                                   int32_t truncation_voxels, float max_weight,
+                                   const float* depth_dev, const tsdf_pinhole* intr,
+                                   const double T_world_cam[16], void* cuda_stream) {
+  if (!buf || !buf->keys || !buf->vals || !buf->mask || !buf->pool || !buf->block_keys ||
+      !buf->counters || !depth_dev || !intr || !T_world_cam)
+    return TSDF_ERR_ARG;
+  if (!(voxel_size > 0.0f) || !std::isfinite(voxel_size) || truncation_voxels <= 0 ||
+      !(max_weight > 0.0f) || !std::isfinite(max_weight))
+    return TSDF_ERR_ARG;
+  if (buf->max_blocks <= 0) return TSDF_ERR_ARG;
+  if (buf->max_blocks > kStaticMaxBlocks) return TSDF_ERR_CAPACITY;  // beyond the scratch size
+  const int64_t cap = buf->hash_capacity;
+  if (cap < 2 * buf->max_blocks || cap > (1ll << 30) || (cap & (cap - 1)) != 0) return TSDF_ERR_ARG;
+  uint32_t* scratch = nullptr;
+  tsdf_status st = static_scratch(&scratch);
+  if (st != TSDF_OK) return st;
+
+  BatchParams<1, 1> p;
+  std::memset(&p, 0, sizeof(p));
+  p.n_frames = 1;
+  p.n_maps = 1;
+  MapDev& d = p.maps[0];
+  d.keys = buf->keys;
+  d.vals = buf->vals;
+  d.mask = buf->mask;
+  d.pool = buf->pool;
+  d.block_keys = buf->block_keys;
+  d.counters = buf->counters;
+  d.list = scratch;
+  d.ctl = scratch + kStaticMaxBlocks;
+  d.list_cap = (uint32_t)buf->max_blocks;
+  d.cap_mask = (uint32_t)(cap - 1);
+  d.max_blocks = (int32_t)buf->max_blocks;
+  d.storage = TSDF_STORAGE_FP32;
+  d.lidar_nearest = 0;
+  d.v = voxel_size;
+  d.tau = (float)((double)truncation_voxels * (double)voxel_size);
+  d.inv_tau = 1.0f / d.tau;
+  d.wmax = max_weight;
+  d.guard = d.tau;
+
+  FrameDev& F = p.fr[0];
+  if (!rigid(T_world_cam) || !valid_pinhole(intr)) return TSDF_ERR_ARG;
+  F.kind = TSDF_SENSOR_PINHOLE;
+  F.map = 0;
+  F.depth = depth_dev;
+  F.width = intr->width;
+  F.height = intr->height;
+  F.fu = intr->fu;
+  F.fv = intr->fv;
+  F.cu = intr->cu;
+  F.cv = intr->cv;
+  F.blk_begin = 0;
+  F.bit = 0;
+  if (!prepare_pose(8.0 * (double)voxel_size, T_world_cam, F)) return TSDF_ERR_ARG;
+
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cuda_fail();
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // the control words must start at zero; a previous call leaves them so,
+  // but a call that never ran to completion might not have
+  if (cudaMemsetAsync(d.ctl, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return cuda_fail();
+  const int th = pick_tile_h((int64_t)F.width * F.height);
+  if (gbt::launch_band_alloc(p, alloc_ctas(F, th), th, s) != cudaSuccess) return cuda_fail();
+  if (gbt::launch_integrate(p, std::max(1, sms) * gbt::integrate_ctas_per_sm(TSDF_STORAGE_FP32), s) !=
+      cudaSuccess)
+    return cuda_fail();
+  return TSDF_OK;
+}
+
+}  // extern "C"
