@@ -34,6 +34,17 @@ UNIT = "voxel updates/s"
 WORKLOAD = "room 10x10x3 m, 300 frames 640x480 f=525, voxel 0.02 m, trunc 4 voxels, max weight 100"
 
 
+# GB300: 152 SMs x 128 FP32/INT32 lanes at the 2070 MHz maximum SM clock
+ALU_PEAK_OPS = 152 * 128 * 2.070e9
+# algorithmic ALU operations of the allocator's prescribed decision sequence:
+# per band segment (ray direction 6, band ends 3, start point 3, range check 3,
+# floor and convert 6, three axes x (sign 2, reciprocal 1, boundary 1,
+# crossing 2) = 18, key 7) and per emitted cell (axis choice 4, end test 2,
+# advance 4, duplicate check 2)
+OPS_PER_SEGMENT = 46
+OPS_PER_CELL = 12
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -41,6 +52,29 @@ def _peaks():
         return float(pk["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def _kernel_rev() -> str:
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2311_00626_gb300", "csrc", "kernels.cu"), "rb") as fh:
+        return hashlib.sha1(fh.read()).hexdigest()[:12]
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu record, if it
+    was taken on the current kernels.cu; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    try:
+        rev = _kernel_rev()
+        with open(path) as fh:
+            for line in fh:
+                f = line.split()
+                if (len(f) >= 3 and not line.startswith("#") and f[0] == rev
+                        and f[1].split("<")[0] == kernel):
+                    return float(f[2])
+    except OSError:
+        pass
+    return None
 
 
 class ClockSampler:
@@ -166,7 +200,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=8, help="frames per integrate_batch launch")
+    ap.add_argument("--batch", type=int, default=32, help="frames per integrate_batch launch")
     ap.add_argument("--ref-frames", type=int, default=150)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
@@ -248,14 +282,19 @@ def main():
     launches_per_step = st["launches"]
     visits = st["block_visits"]
     fresh = st["blocks"]
-    # algorithmic bytes of one integration launch: every listed block read and
-    # written once (fresh blocks only written), plus the depth images it reads
+    # integration kernel, HBM roofline: every listed block read and written
+    # once per launch (fresh blocks only written), plus the depth images
     block_bytes = 512 * 8
     bytes_per_step = (2 * visits - fresh) * block_bytes + in_bytes
     integ_bytes_per_launch = bytes_per_step / launches_per_step
     integ_ms_per_launch = integ_ms / max(calls, 1)
     hbm_peak, peak_src = _peaks()
     achieved = integ_bytes_per_launch / (integ_ms_per_launch * 1e-3) / 1e9
+    # allocation kernel, ALU roofline: algorithmic operations of its walks
+    alloc_ms_per_launch = alloc_ms / max(calls, 1)
+    alloc_ops_per_launch = (OPS_PER_SEGMENT * st["segments"] + OPS_PER_CELL * st["cells"]) / launches_per_step
+    alloc_achieved = alloc_ops_per_launch / (alloc_ms_per_launch * 1e-3)
+    alloc_share = alloc_ms / max(alloc_ms + integ_ms, 1e-9)
     value = ws * updates_per_step / (ms * 1e-3)
     fps = ws * n_frames / (ms * 1e-3)
 
@@ -334,12 +373,22 @@ def main():
                        "l2": f"inputs {in_bytes / 1e6:.0f} MB resident in HBM (> 129 MB L2)",
                        "parallelism": f"replicas x{ws}"},
             "frames_per_s": fps,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
-                         "kernel": "integrate_kernel", "peak_source": peak_src,
-                         "bytes_per_launch": integ_bytes_per_launch,
-                         "ms_per_launch": integ_ms_per_launch,
-                         "alloc_ms_per_launch": alloc_ms / max(calls, 1)},
+            "roofline": {"bound": "alu", "achieved": alloc_achieved / 1e12,
+                         "peak": ALU_PEAK_OPS / 1e12, "unit": "Tops/s",
+                         "frac": alloc_achieved / ALU_PEAK_OPS,
+                         "traffic": _traffic("band_alloc_kernel"),
+                         "kernel": "band_alloc_kernel", "share_of_kernel_time": alloc_share,
+                         "peak_source": "152 SMs x 128 lanes x 2070 MHz",
+                         "ops_per_launch": alloc_ops_per_launch,
+                         "ms_per_launch": alloc_ms_per_launch,
+                         "segments_per_step": st["segments"], "cells_per_step": st["cells"]},
+            "roofline_integrate": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                                   "unit": "GB/s", "frac": achieved / hbm_peak,
+                                   "traffic": _traffic("integrate_kernel"),
+                                   "kernel": "integrate_kernel", "peak_source": peak_src,
+                                   "share_of_kernel_time": 1.0 - alloc_share,
+                                   "bytes_per_launch": integ_bytes_per_launch,
+                                   "ms_per_launch": integ_ms_per_launch},
             "kernel_ms_per_step": {"band_alloc": alloc_ms / args.steps,
                                    "integrate": integ_ms / args.steps},
             "e2e": {"value": ws * updates_per_step / (e2e_ms * 1e-3), "unit": UNIT,

@@ -173,8 +173,10 @@ tsdf_status map_num_blocks(const tsdf_map* map, int64_t* out);
  * out[0] blocks allocated, out[1] voxel updates (voxel, frame pairs that
  * passed the update test), out[2] frames integrated, out[3] sticky device
  * status bits, out[4] block visits (blocks listed by integration launches,
- * summed over launches), out[5] integration launches. */
-tsdf_status map_stats(const tsdf_map* map, int64_t out[6]);
+ * summed over launches), out[5] integration launches, out[6] band segments
+ * walked (valid pixels), out[7] block-grid cells emitted by those walks
+ * (counting a block once per pixel that meets it). */
+tsdf_status map_stats(const tsdf_map* map, int64_t out[8]);
 
 /* map_timing — diagnostics: while enabled, every integrate call on this map
  * (or integrate_batch whose first map it is) records CUDA events around its

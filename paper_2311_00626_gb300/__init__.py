@@ -203,10 +203,11 @@ def map_num_blocks(m: int) -> int:
 
 
 def map_stats(m: int) -> dict:
-    out = np.zeros(6, np.int64)
+    out = np.zeros(8, np.int64)
     _check(lib().map_stats(m, out.ctypes.data_as(ctypes.c_void_p)), "map_stats")
     return {"blocks": int(out[0]), "voxel_updates": int(out[1]), "frames": int(out[2]),
-            "status_bits": int(out[3]), "block_visits": int(out[4]), "launches": int(out[5])}
+            "status_bits": int(out[3]), "block_visits": int(out[4]), "launches": int(out[5]),
+            "segments": int(out[6]), "cells": int(out[7])}
 
 
 def map_timing(m: int, enable: bool = True):

@@ -221,6 +221,7 @@ template <int NF, int NM, int TH>
 __global__ void __launch_bounds__(kAllocThreads)
     band_alloc_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
   constexpr int kRows = TH * kTileW / kAllocThreads;  // pixel rows per thread
+  uint32_t segs = 0, cells = 0;                        // walk statistics
   __shared__ uint32_t s_set[kSetSize];
   __shared__ uint32_t s_keys[kSetSize];
   __shared__ uint32_t s_nkeys;
@@ -276,9 +277,11 @@ __global__ void __launch_bounds__(kAllocThreads)
         live = true;
       }
     }
+    segs += live ? 1u : 0u;
     while (__any_sync(0xffffffffu, live)) {
       const uint32_t left = __shfl_up_sync(0xffffffffu, wk.key, 1);
       if (live) {
+        ++cells;
         if (wk.key & kFarFlag) {
           claim_block(m, rel_to_key(wk.key & ~kFarFlag, F.a, b0x, b0y, b0z), F.bit);
         } else if (!(lane > 0 && left == wk.key) && !set_insert(s_set, wk.key)) {
@@ -298,6 +301,16 @@ __global__ void __launch_bounds__(kAllocThreads)
   __syncthreads();
   const uint32_t nk = s_nkeys;
   for (uint32_t i = threadIdx.x; i < nk; i += kAllocThreads) claim_block(m, rel_to_key(s_keys[i], F.a), F.bit);
+  if (m.walk_stats) {
+    for (int o = 16; o > 0; o >>= 1) {
+      segs += __shfl_down_sync(0xffffffffu, segs, o);
+      cells += __shfl_down_sync(0xffffffffu, cells, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(m.counters + kCntSegments, (unsigned long long)segs);
+      atomicAdd(m.counters + kCntCells, (unsigned long long)cells);
+    }
+  }
 }
 
 // ------------------------------------------------ per-voxel projection
@@ -570,8 +583,9 @@ __global__ void __launch_bounds__(kIntegrateThreads)
       uint32_t bits = slot_mask;
       while (bits) {
         // bit k of the mask is frame k of the batch; frames apply in batch
-        // order.  Runs of up to four pinhole frames issue all their depth
-        // loads before the first update.
+        // order.  A run of four pinhole frames issues all its depth loads
+        // before the first update; shorter runs go frame by frame (fewer
+        // code paths keep the kernel small in the instruction cache).
         int fq[4];
         int nq = 0;
         bool go = true;
@@ -590,9 +604,12 @@ __global__ void __launch_bounds__(kIntegrateThreads)
           }
         }
         if (nq == 4) fuse_pinhole<4>(p, fq, m, vr, D, W, my_upd);
-        else if (nq == 3) fuse_pinhole<3>(p, fq, m, vr, D, W, my_upd);
-        else if (nq == 2) fuse_pinhole<2>(p, fq, m, vr, D, W, my_upd);
-        else if (nq == 1) fuse_pinhole<1>(p, fq, m, vr, D, W, my_upd);
+        else if (nq >= 1) {
+          for (int q = 0; q < nq; ++q) {
+            const int fq1[4] = {fq[q], -1, -1, -1};
+            fuse_pinhole<1>(p, fq1, m, vr, D, W, my_upd);
+          }
+        }
         else {
           const int f = __ffs(bits) - 1;  // a LiDAR frame
           bits &= bits - 1u;

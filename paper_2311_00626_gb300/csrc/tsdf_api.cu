@@ -291,6 +291,7 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   d.list_cap = (uint32_t)o.max_blocks;
   d.storage = o.storage;
   d.lidar_nearest = o.lidar_nearest ? 1 : 0;
+  d.walk_stats = 1;
   d.v = voxel_size;
   d.tau = (float)((double)truncation_voxels * m->vd);
   d.inv_tau = 1.0f / d.tau;
@@ -407,7 +408,7 @@ tsdf_status map_num_blocks(const tsdf_map* map, int64_t* out) {
   return TSDF_OK;
 }
 
-tsdf_status map_stats(const tsdf_map* map, int64_t out[6]) {
+tsdf_status map_stats(const tsdf_map* map, int64_t out[8]) {
   if (!map || !out) return TSDF_ERR_ARG;
   unsigned long long c[gbt::kNumCounters];
   tsdf_status st = read_counters(map, c);
@@ -418,6 +419,8 @@ tsdf_status map_stats(const tsdf_map* map, int64_t out[6]) {
   out[3] = (int64_t)map->status_seen;
   out[4] = (int64_t)c[gbt::kCntVisits];
   out[5] = (int64_t)c[gbt::kCntLaunches];
+  out[6] = (int64_t)c[gbt::kCntSegments];
+  out[7] = (int64_t)c[gbt::kCntCells];
   return TSDF_OK;
 }
 

@@ -32,7 +32,9 @@ enum : int {
   kCntStatus = 2,   // sticky status bits
   kCntVisits = 3,   // work-list entries consumed by integration launches
   kCntLaunches = 4, // integration launches
-  kNumCounters = 6
+  kCntSegments = 5, // band segments walked by the allocator (valid pixels in range)
+  kCntCells = 6,    // cells emitted by those walks (with repeats across pixels)
+  kNumCounters = 8
 };
 // Sticky status bits.
 enum : unsigned long long { kStPoolFull = 1, kStHashFull = 2, kStListFull = 4, kStTimeout = 8 };
@@ -51,7 +53,9 @@ struct MapDev {
   uint32_t* mask;                 // [cap] frames of the current batch meeting the block
   void* pool;                     // [max_blocks][512] float2 {D, W} or __half2 {D/tau, W}
   unsigned long long* block_keys; // [max_blocks] key of each pool block
-  unsigned long long* counters;   // [kNumCounters]
+  unsigned long long* counters;   // [kNumCounters]; entries from kCntSegments on only
+                                  // when walk_stats != 0
+  int32_t walk_stats;             // count band segments and cells
   uint32_t* list;                 // [list_cap] slots met by the current batch
   unsigned int* ctl;              // [0] list length, [1] finished integration CTAs,
                                   // [2] entries handed out (first map of a batch)

@@ -9,10 +9,13 @@ def run_oracle(frames, voxel_size, trunc=4, wmax=100.0, lidar_nearest=False, gua
     m = oracle.OracleMap(voxel_size, trunc, wmax)
     if lidar_nearest or guard:
         m.set_lidar_sampling(lidar_nearest, guard)
+    cells = 0
     for f in frames:
         m.integrate(f.sensor, f.T, f.depth)
+        cells += m.counters()["candidates"]
     out = m.export()
     counters = m.counters()
+    counters["total_cells"] = cells
     m.close()
     return out, counters
 

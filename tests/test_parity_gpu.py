@@ -57,6 +57,8 @@ def _parity(name, frames, v, tol, **kw):
     assert status == 0, f"device status {status}"
     st = compare(gpu, orc, tol, name)
     assert gs["voxel_updates"] == oc["total_updates"], (gs, oc)
+    # the allocator emitted exactly the oracle's cells (same walks)
+    assert gs["cells"] == oc["total_cells"], (gs, oc)
     _record(name, st)
     return st
 
