@@ -82,13 +82,19 @@ enum { TSDF_SENSOR_PINHOLE = 0, TSDF_SENSOR_LIDAR = 1 };
  * at least 2 * max_blocks (0 = that minimum).  lidar_nearest != 0 samples
  * LiDAR images at the nearest beam instead of guarded bilinear;
  * lidar_guard is the bilinear foreground/background threshold in metres
- * (<= 0: the truncation distance). */
+ * (<= 0: the truncation distance).  Launch-shape knobs (results do not
+ * depend on them): alloc_tile_h is the pixel-tile height of the allocation
+ * kernel, 16 or 32 (0 = chosen from the pixels per launch);
+ * integrate_ctas_per_sm is the integration kernel's resident CTAs per SM
+ * (0 = as many as fit).  For integrate_batch the first map's knobs apply. */
 typedef struct {
   int32_t storage;
   int64_t max_blocks;
   int64_t hash_capacity;
   int32_t lidar_nearest;
   float lidar_guard;
+  int32_t alloc_tile_h;
+  int32_t integrate_ctas_per_sm;
 } tsdf_map_opts;
 
 /* One frame of a batch.  `map` indexes the maps array of integrate_batch;

@@ -56,7 +56,8 @@ class Lidar(ctypes.Structure):
 class MapOpts(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int32), ("max_blocks", ctypes.c_int64),
                 ("hash_capacity", ctypes.c_int64), ("lidar_nearest", ctypes.c_int32),
-                ("lidar_guard", ctypes.c_float)]
+                ("lidar_guard", ctypes.c_float), ("alloc_tile_h", ctypes.c_int32),
+                ("integrate_ctas_per_sm", ctypes.c_int32)]
 
 
 class FrameDesc(ctypes.Structure):
@@ -160,9 +161,11 @@ def map_create(voxel_size: float, truncation_voxels: int, max_weight: float) -> 
 
 
 def map_create_ex(voxel_size, truncation_voxels, max_weight, storage=STORAGE_FP32, max_blocks=0,
-                  hash_capacity=0, lidar_nearest=False, lidar_guard=0.0) -> int:
+                  hash_capacity=0, lidar_nearest=False, lidar_guard=0.0, alloc_tile_h=0,
+                  integrate_ctas_per_sm=0) -> int:
     h = ctypes.c_void_p()
-    o = MapOpts(storage, max_blocks, hash_capacity, int(lidar_nearest), lidar_guard)
+    o = MapOpts(storage, max_blocks, hash_capacity, int(lidar_nearest), lidar_guard, alloc_tile_h,
+                integrate_ctas_per_sm)
     _check(lib().map_create_ex(voxel_size, truncation_voxels, max_weight, ctypes.byref(o),
                                ctypes.byref(h)), "map_create_ex")
     return h.value
@@ -257,9 +260,11 @@ class TsdfMap:
 
     def __init__(self, voxel_size: float, truncation_voxels: int = 4, max_weight: float = 100.0,
                  storage: int = STORAGE_FP32, max_blocks: int = 0, hash_capacity: int = 0,
-                 lidar_nearest: bool = False, lidar_guard: float = 0.0):
+                 lidar_nearest: bool = False, lidar_guard: float = 0.0, alloc_tile_h: int = 0,
+                 integrate_ctas_per_sm: int = 0):
         self.handle = map_create_ex(voxel_size, truncation_voxels, max_weight, storage,
-                                    max_blocks, hash_capacity, lidar_nearest, lidar_guard)
+                                    max_blocks, hash_capacity, lidar_nearest, lidar_guard,
+                                    alloc_tile_h, integrate_ctas_per_sm)
         self.voxel_size = voxel_size
         self.storage = storage
 

@@ -34,6 +34,7 @@ struct tsdf_map {
   int32_t trunc;
   double vd, Bd;
   int n_ctas_integrate;
+  int tile_h;  // allocation tile height, 0 = automatic
   int64_t frames;
   unsigned long long status_seen;  // device status bits observed by the host
   std::vector<LidarTable> tables;
@@ -217,7 +218,7 @@ tsdf_status integrate_one(tsdf_map* m, int kind, const tsdf_pinhole* ph, const t
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t* ev = timing_slot(m);
   if (ev) cudaEventRecord(ev[0], s);
-  const int th = pick_tile_h((int64_t)p.fr[0].width * p.fr[0].height);
+  const int th = m->tile_h ? m->tile_h : pick_tile_h((int64_t)p.fr[0].width * p.fr[0].height);
   if (gbt::launch_band_alloc(p, alloc_ctas(p.fr[0], th), th, s) != cudaSuccess) return cuda_fail();
   if (ev) cudaEventRecord(ev[1], s);
   if (gbt::launch_integrate(p, m->n_ctas_integrate, s) != cudaSuccess) return cuda_fail();
@@ -258,8 +259,11 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   if (!out || !(voxel_size > 0.0f) || !std::isfinite(voxel_size) || truncation_voxels <= 0 ||
       !(max_weight > 0.0f) || !std::isfinite(max_weight))
     return TSDF_ERR_ARG;
-  tsdf_map_opts o{TSDF_STORAGE_FP32, kDefaultBlocks, 0, 0, 0.0f};
+  tsdf_map_opts o{TSDF_STORAGE_FP32, kDefaultBlocks, 0, 0, 0.0f, 0, 0};
   if (opts) o = *opts;
+  if (o.alloc_tile_h != 0 && o.alloc_tile_h != gbt::kTileHSmall && o.alloc_tile_h != gbt::kTileHBig)
+    return TSDF_ERR_ARG;
+  if (o.integrate_ctas_per_sm < 0) return TSDF_ERR_ARG;
   if (o.storage != TSDF_STORAGE_FP32 && o.storage != TSDF_STORAGE_FP16) return TSDF_ERR_ARG;
   if (o.max_blocks <= 0) o.max_blocks = kDefaultBlocks;
   if (o.max_blocks > (1ll << 27)) return TSDF_ERR_ARG;
@@ -313,7 +317,10 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
-  m->n_ctas_integrate = std::max(1, sms) * gbt::integrate_ctas_per_sm(o.storage);
+  int per_sm = gbt::integrate_ctas_per_sm(o.storage);
+  if (o.integrate_ctas_per_sm > 0) per_sm = std::min(per_sm, o.integrate_ctas_per_sm);
+  m->n_ctas_integrate = std::max(1, sms) * per_sm;
+  m->tile_h = o.alloc_tile_h;
   *out = m;
   return TSDF_OK;
 }
@@ -351,10 +358,8 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
   p.n_frames = n;
   p.n_maps = n_maps;
   int ctas = 0, integ = 1;
-  for (int i = 0; i < n_maps; ++i) {
-    p.maps[i] = maps[i]->dev;
-    integ = std::max(integ, maps[i]->n_ctas_integrate);
-  }
+  for (int i = 0; i < n_maps; ++i) p.maps[i] = maps[i]->dev;
+  integ = maps[0]->n_ctas_integrate;
   int64_t pixels = 0;
   for (int f = 0; f < n; ++f) {
     const tsdf_frame_desc& fd = frames[f];
@@ -365,7 +370,7 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
     p.fr[f].bit = f;
     pixels += (int64_t)p.fr[f].width * p.fr[f].height;
   }
-  const int th = pick_tile_h(pixels);
+  const int th = maps[0]->tile_h ? maps[0]->tile_h : pick_tile_h(pixels);
   for (int f = 0; f < n; ++f) {
     p.fr[f].blk_begin = ctas;
     ctas += alloc_ctas(p.fr[f], th);

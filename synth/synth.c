@@ -149,12 +149,51 @@ static double hit_plane(const double* p, const double o[3], const double d[3]) {
   return t > kEps ? t : INFINITY;
 }
 
-/* First hit parameter t > 0 of o + t d against every primitive, or INFINITY. */
+/* Bounding sphere of a bounded solid (boxes, spheres, cylinders): centre c,
+ * squared radius; returns 0 for unbounded primitives (rooms, planes). */
+static int bound(const double* q, double c[3], double* r2) {
+  const double* p = q + 1;
+  switch ((int)q[0]) {
+    case SYN_BOX:
+      for (int k = 0; k < 3; ++k) c[k] = 0.5 * (p[k] + p[3 + k]);
+      *r2 = 0.25 * ((p[3] - p[0]) * (p[3] - p[0]) + (p[4] - p[1]) * (p[4] - p[1]) + (p[5] - p[2]) * (p[5] - p[2]));
+      return 1;
+    case SYN_SPHERE:
+      c[0] = p[0]; c[1] = p[1]; c[2] = p[2];
+      *r2 = p[3] * p[3];
+      return 1;
+    case SYN_CYL: {
+      const double h = 0.5 * (p[4] - p[3]);
+      c[0] = p[0]; c[1] = p[1]; c[2] = 0.5 * (p[3] + p[4]);
+      *r2 = p[2] * p[2] + h * h;
+      return 1;
+    }
+    default:
+      return 0;
+  }
+}
+
+/* First hit parameter t > 0 of o + t d against every primitive, or INFINITY.
+ * Bounded solids whose bounding sphere the ray misses (or meets only beyond
+ * the best hit so far) are skipped; the exact tests decide everything else. */
 double synth_cast(const double* prims, int32_t n, const double o[3], const double d[3]) {
   double best = INFINITY;
+  const double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
   for (int32_t i = 0; i < n; ++i) {
     const double* q = prims + (size_t)i * SYN_NPAR;
     const double* p = q + 1;
+    double c[3], r2;
+    if (bound(q, c, &r2)) {
+      const double oc[3] = {c[0] - o[0], c[1] - o[1], c[2] - o[2]};
+      const double ocd = oc[0] * d[0] + oc[1] * d[1] + oc[2] * d[2];
+      const double oc2 = oc[0] * oc[0] + oc[1] * oc[1] + oc[2] * oc[2];
+      if (oc2 > r2 * 1.0000001 + 1e-12) {  /* origin outside the sphere */
+        if (ocd <= 0) continue;                                /* sphere behind the ray */
+        if (oc2 - ocd * ocd / dd > r2 * 1.0000001 + 1e-12) continue;  /* ray misses it */
+        const double tnear = (ocd - sqrt(r2 * dd)) / dd;       /* lower bound on any hit */
+        if (tnear > best) continue;
+      }
+    }
     double t = INFINITY;
     switch ((int)q[0]) {
       case SYN_ROOM: t = hit_room(p, o, d); break;
