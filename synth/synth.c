@@ -149,6 +149,18 @@ static double hit_plane(const double* p, const double o[3], const double d[3]) {
   return t > kEps ? t : INFINITY;
 }
 
+static double hit_prim(const double* q, const double o[3], const double d[3]) {
+  const double* p = q + 1;
+  switch ((int)q[0]) {
+    case SYN_ROOM: return hit_room(p, o, d);
+    case SYN_BOX: return hit_box(p, o, d);
+    case SYN_SPHERE: return hit_sphere(p, o, d);
+    case SYN_CYL: return hit_cyl(p, o, d);
+    case SYN_PLANE: return hit_plane(p, o, d);
+    default: return INFINITY;
+  }
+}
+
 /* Bounding sphere of a bounded solid (boxes, spheres, cylinders): centre c,
  * squared radius; returns 0 for unbounded primitives (rooms, planes). */
 static int bound(const double* q, double c[3], double* r2) {
@@ -194,16 +206,143 @@ double synth_cast(const double* prims, int32_t n, const double o[3], const doubl
         if (tnear > best) continue;
       }
     }
-    double t = INFINITY;
-    switch ((int)q[0]) {
-      case SYN_ROOM: t = hit_room(p, o, d); break;
-      case SYN_BOX: t = hit_box(p, o, d); break;
-      case SYN_SPHERE: t = hit_sphere(p, o, d); break;
-      case SYN_CYL: t = hit_cyl(p, o, d); break;
-      case SYN_PLANE: t = hit_plane(p, o, d); break;
-      default: break;
-    }
+    const double t = hit_prim(q, o, d);
     if (t < best) best = t;
+  }
+  return best;
+}
+
+/* --------------------------------------------------- 2D grid acceleration */
+
+/* Uniform grid over the xy extent of the bounded solids: each cell lists the
+ * solids whose xy bounding box (grown by 1e-6 m) overlaps it; rooms and
+ * planes are tested for every ray.  A ray walks the cells its xy projection
+ * crosses and stops once its best hit lies before the next cell; the exact
+ * hit tests decide, so images equal those of the exhaustive caster. */
+typedef struct {
+  double x0, y0, cell;
+  int nx, ny;
+  int* start;   /* [nx*ny + 1] */
+  int* items;
+  int* unb;     /* unbounded primitives */
+  int n_unb;
+} grid2;
+
+static int xy_box(const double* q, double b[4]) {
+  const double* p = q + 1;
+  switch ((int)q[0]) {
+    case SYN_BOX: b[0] = p[0]; b[1] = p[1]; b[2] = p[3]; b[3] = p[4]; return 1;
+    case SYN_SPHERE: b[0] = p[0] - p[3]; b[1] = p[1] - p[3]; b[2] = p[0] + p[3]; b[3] = p[1] + p[3]; return 1;
+    case SYN_CYL: b[0] = p[0] - p[2]; b[1] = p[1] - p[2]; b[2] = p[0] + p[2]; b[3] = p[1] + p[2]; return 1;
+    default: return 0;
+  }
+}
+
+static void grid_free(grid2* g) {
+  free(g->start);
+  free(g->items);
+  free(g->unb);
+}
+
+static int grid_build(grid2* g, const double* prims, int32_t n) {
+  memset(g, 0, sizeof(*g));
+  double lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
+  int nb = 0;
+  g->unb = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+  for (int32_t i = 0; i < n; ++i) {
+    double b[4];
+    if (!xy_box(prims + (size_t)i * SYN_NPAR, b)) { g->unb[g->n_unb++] = i; continue; }
+    ++nb;
+    if (b[0] < lo[0]) lo[0] = b[0];
+    if (b[1] < lo[1]) lo[1] = b[1];
+    if (b[2] > hi[0]) hi[0] = b[2];
+    if (b[3] > hi[1]) hi[1] = b[3];
+  }
+  if (nb == 0) { g->nx = g->ny = 0; g->start = NULL; g->items = NULL; return 0; }
+  const double ext = fmax(hi[0] - lo[0], hi[1] - lo[1]);
+  g->cell = fmax(ext / 48.0, 0.25);
+  g->x0 = lo[0] - 1e-3;
+  g->y0 = lo[1] - 1e-3;
+  g->nx = (int)((hi[0] - g->x0) / g->cell) + 1;
+  g->ny = (int)((hi[1] - g->y0) / g->cell) + 1;
+  const int nc = g->nx * g->ny;
+  g->start = (int*)calloc((size_t)nc + 1, sizeof(int));
+  for (int pass = 0; pass < 2; ++pass) {
+    int* fill = NULL;
+    if (pass == 1) {
+      for (int c = 0; c < nc; ++c) g->start[c + 1] += g->start[c];
+      g->items = (int*)malloc(sizeof(int) * (g->start[nc] > 0 ? g->start[nc] : 1));
+      fill = (int*)calloc((size_t)nc, sizeof(int));
+    }
+    for (int32_t i = 0; i < n; ++i) {
+      double b[4];
+      if (!xy_box(prims + (size_t)i * SYN_NPAR, b)) continue;
+      int cx0 = (int)floor((b[0] - 1e-6 - g->x0) / g->cell), cx1 = (int)floor((b[2] + 1e-6 - g->x0) / g->cell);
+      int cy0 = (int)floor((b[1] - 1e-6 - g->y0) / g->cell), cy1 = (int)floor((b[3] + 1e-6 - g->y0) / g->cell);
+      if (cx0 < 0) cx0 = 0;
+      if (cy0 < 0) cy0 = 0;
+      if (cx1 >= g->nx) cx1 = g->nx - 1;
+      if (cy1 >= g->ny) cy1 = g->ny - 1;
+      for (int cy = cy0; cy <= cy1; ++cy)
+        for (int cx = cx0; cx <= cx1; ++cx) {
+          const int c = cy * g->nx + cx;
+          if (pass == 0) g->start[c + 1]++;
+          else g->items[g->start[c] + fill[c]++] = i;
+        }
+    }
+    free(fill);
+  }
+  return 1;
+}
+
+/* mark[i] == stamp: primitive i already tested for this ray */
+static double grid_cast(const grid2* g, const double* prims, const double o[3], const double d[3],
+                        int* mark, int stamp) {
+  double best = INFINITY;
+  for (int k = 0; k < g->n_unb; ++k) {
+    const double t = hit_prim(prims + (size_t)g->unb[k] * SYN_NPAR, o, d);
+    if (t < best) best = t;
+  }
+  if (g->nx == 0) return best;
+  /* clip the ray's xy projection to the grid rectangle */
+  double t0 = 0.0, t1 = INFINITY;
+  const double lo[2] = {g->x0, g->y0}, hi[2] = {g->x0 + g->nx * g->cell, g->y0 + g->ny * g->cell};
+  for (int k = 0; k < 2; ++k) {
+    if (d[k] == 0.0) {
+      if (o[k] < lo[k] || o[k] > hi[k]) return best;
+      continue;
+    }
+    double a = (lo[k] - o[k]) / d[k], b = (hi[k] - o[k]) / d[k];
+    if (a > b) { const double s = a; a = b; b = s; }
+    if (a > t0) t0 = a;
+    if (b < t1) t1 = b;
+  }
+  if (!(t0 <= t1) || t0 >= best) return best;
+  const double px = o[0] + t0 * d[0], py = o[1] + t0 * d[1];
+  int cx = (int)floor((px - g->x0) / g->cell), cy = (int)floor((py - g->y0) / g->cell);
+  if (cx < 0) cx = 0;
+  if (cx >= g->nx) cx = g->nx - 1;
+  if (cy < 0) cy = 0;
+  if (cy >= g->ny) cy = g->ny - 1;
+  const int sx = d[0] > 0 ? 1 : (d[0] < 0 ? -1 : 0), sy = d[1] > 0 ? 1 : (d[1] < 0 ? -1 : 0);
+  double tx = INFINITY, ty = INFINITY, dtx = INFINITY, dty = INFINITY;
+  if (sx) { tx = (g->x0 + (cx + (sx > 0)) * g->cell - o[0]) / d[0]; dtx = g->cell / fabs(d[0]); }
+  if (sy) { ty = (g->y0 + (cy + (sy > 0)) * g->cell - o[1]) / d[1]; dty = g->cell / fabs(d[1]); }
+  for (;;) {
+    const int c = cy * g->nx + cx;
+    for (int k = g->start[c]; k < g->start[c + 1]; ++k) {
+      const int i = g->items[k];
+      if (mark[i] == stamp) continue;
+      mark[i] = stamp;
+      const double t = hit_prim(prims + (size_t)i * SYN_NPAR, o, d);
+      if (t < best) best = t;
+    }
+    const double tn = tx < ty ? tx : ty;
+    /* a hit before the next cell cannot be beaten by solids met later
+       (their hits lie at or beyond the cell boundary, up to the 1e-6 margin) */
+    if (best < tn - 1e-5 || tn > t1) break;
+    if (tx < ty) { cx += sx; tx += dtx; } else { cy += sy; ty += dty; }
+    if (cx < 0 || cx >= g->nx || cy < 0 || cy >= g->ny) break;
   }
   return best;
 }
@@ -221,20 +360,25 @@ void synth_render_pinhole(const double* prims, int32_t n, const double T[16], do
                           double invalid_frac, double max_depth, uint64_t seed, uint64_t frame,
                           float* out) {
   const double o[3] = {T[3], T[7], T[11]};
-#pragma omp parallel for schedule(static)
+  grid2 g;
+  grid_build(&g, prims, n);
+#pragma omp parallel for schedule(dynamic, 4)
   for (int32_t j = 0; j < H; ++j) {
+    int* mark = (int*)calloc((size_t)(n > 0 ? n : 1), sizeof(int));
     for (int32_t i = 0; i < W; ++i) {
       double rc[3] = {((double)i - cu) / fu, ((double)j - cv) / fv, 1.0};
       double dw[3];
       for (int k = 0; k < 3; ++k) dw[k] = T[4 * k + 0] * rc[0] + T[4 * k + 1] * rc[1] + T[4 * k + 2] * rc[2];
-      double z = synth_cast(prims, n, o, dw);
+      double z = grid_cast(&g, prims, o, dw, mark, i + 1);
       uint64_t pix = (uint64_t)j * (uint64_t)W + (uint64_t)i;
       if (isfinite(z) && sigma_z2 > 0) z += ctr_normal(seed, frame, pix) * sigma_z2 * z * z;
       if (invalid_frac > 0 && u01(ctr_hash(seed, frame, pix, 3)) < invalid_frac) z = 0;
       if (!isfinite(z) || z <= 0 || z > max_depth) z = 0;
       out[pix] = (float)z;
     }
+    free(mark);
   }
+  grid_free(&g);
 }
 
 /*
@@ -250,21 +394,26 @@ void synth_render_lidar(const double* prims, int32_t n, const double T[16], int3
                         double min_range, double max_range, double sigma, uint64_t seed,
                         uint64_t frame, float* out) {
   const double o[3] = {T[3], T[7], T[11]};
-#pragma omp parallel for schedule(static)
+  grid2 g;
+  grid_build(&g, prims, n);
+#pragma omp parallel for schedule(dynamic, 1)
   for (int32_t j = 0; j < n_el; ++j) {
     double phi = phi_start + ((double)j + 0.5) * (el_fov / (double)n_el);
+    int* mark = (int*)calloc((size_t)(n > 0 ? n : 1), sizeof(int));
     for (int32_t k = 0; k < n_az; ++k) {
       double th = theta_start + ((double)k + 0.5) * (6.283185307179586 / (double)n_az);
       double b[3] = {sin(phi) * cos(th), sin(phi) * sin(th), cos(phi)};
       double dw[3];
       for (int q = 0; q < 3; ++q) dw[q] = T[4 * q + 0] * b[0] + T[4 * q + 1] * b[1] + T[4 * q + 2] * b[2];
-      double r = synth_cast(prims, n, o, dw);
+      double r = grid_cast(&g, prims, o, dw, mark, k + 1);
       uint64_t pix = (uint64_t)j * (uint64_t)n_az + (uint64_t)k;
       if (isfinite(r) && sigma > 0) r += ctr_normal(seed, frame, pix) * sigma;
       if (!isfinite(r) || r < min_range || r > max_range) r = 0;
       out[pix] = (float)r;
     }
+    free(mark);
   }
+  grid_free(&g);
 }
 
 /* ----------------------------------------------------------------- scenes */
