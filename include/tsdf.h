@@ -151,10 +151,14 @@ tsdf_status integrate_lidar(tsdf_map* map, const float* range_dev, const tsdf_li
 
 /*
  * integrate_batch — integrate n frames (any mix of sensors, sizes and maps)
- * with one allocation launch and one integration launch.  The result equals
- * integrating the frames one by one in array order: each map sees its frames
- * in array order.  All maps must have been created on the current device.
- * n <= 32 frames and at most 16 distinct maps per call.
+ * in sub-batches of up to 32 frames, each one allocation launch and one
+ * integration launch; with more than 32 frames the allocation of a
+ * sub-batch overlaps the integration of the previous one (on an internal
+ * stream of the first map, joined back to cuda_stream).  The result equals
+ * integrating the frames one by one in array order (bit for bit with FP32
+ * storage; with FP16 storage a voxel is rounded to FP16 once per sub-batch
+ * instead of once per frame).  All maps must have been created on the
+ * current device; at most 16 distinct maps and 65,536 frames per call.
  */
 tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_frame_desc* frames,
                             int32_t n, void* cuda_stream);
@@ -185,9 +189,9 @@ tsdf_status map_num_blocks(const tsdf_map* map, int64_t* out);
 tsdf_status map_stats(const tsdf_map* map, int64_t out[8]);
 
 /* map_timing — diagnostics: while enabled, every integrate call on this map
- * (or integrate_batch whose first map it is) records CUDA events around its
- * allocation and integration kernels, for up to 4096 calls.  Enabling creates
- * the events; call it outside any timed region. */
+ * (or integrate_batch sub-batch whose first map it is) records CUDA events
+ * around its allocation and integration kernels, for up to 4096 calls.
+ * Enabling creates the events; call it outside any timed region. */
 tsdf_status map_timing(tsdf_map* map, int32_t enable);
 
 /* map_kernel_times — waits for the recorded calls and returns the summed

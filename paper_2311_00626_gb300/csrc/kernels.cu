@@ -136,19 +136,19 @@ struct Walk32 {
     const bool sz_ = tz < t01;
     const float t = sz_ ? tz : t01;
     if (!(t <= s1) || n == kMaxCells) return false;
-    if (sz_) {
-      key += kz;
-      bz += fz;
-      tz = __fmul_rn(__fsub_rn(bz, oz), iz);
-    } else if (sy_) {
-      key += ky;
-      by += fy;
-      ty = __fmul_rn(__fsub_rn(by, oy), iy);
-    } else {
-      key += kx;
-      bx += fx;
-      tx = __fmul_rn(__fsub_rn(bx, ox), ix);
-    }
+    // branch-free: one axis advances, chosen by selects
+    const bool sx_ = !sz_ && !sy_, syy = !sz_ && sy_;
+    key += sz_ ? kz : (sy_ ? ky : kx);
+    bx = sx_ ? bx + fx : bx;
+    by = syy ? by + fy : by;
+    bz = sz_ ? bz + fz : bz;
+    const float bsel = sz_ ? bz : (sy_ ? by : bx);
+    const float osel = sz_ ? oz : (sy_ ? oy : ox);
+    const float isel = sz_ ? iz : (sy_ ? iy : ix);
+    const float tnew = __fmul_rn(__fsub_rn(bsel, osel), isel);
+    tx = sx_ ? tnew : tx;
+    ty = syy ? tnew : ty;
+    tz = sz_ ? tnew : tz;
     ++n;
     return true;
   }
@@ -165,8 +165,16 @@ constexpr uint32_t kFarFlag = 1u << 30;  // key counted from the segment's own s
 // CTA-local set of relative block keys (open addressing in shared memory).
 // Returns false when the key could not be placed within kSetProbes slots;
 // the caller then claims it globally itself.
+__device__ __noinline__ bool set_insert_slow(uint32_t* set, uint32_t key, uint32_t h);
+
 __device__ __forceinline__ bool set_insert(uint32_t* set, uint32_t key) {
-  uint32_t h = (key * 0x9E3779B1u) >> (32 - kSetBits);
+  const uint32_t h = (key * 0x9E3779B1u) >> (32 - kSetBits);
+  // common case: the key is already at its home slot
+  if (((volatile uint32_t*)set)[h] == key) return true;
+  return set_insert_slow(set, key, h);
+}
+
+__device__ __noinline__ bool set_insert_slow(uint32_t* set, uint32_t key, uint32_t h) {
   volatile uint32_t* vs = set;
 #pragma unroll 1
   for (int probe = 0; probe < kSetProbes; ++probe) {

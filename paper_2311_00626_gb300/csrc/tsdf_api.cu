@@ -38,7 +38,14 @@ struct tsdf_map {
   int64_t frames;
   unsigned long long status_seen;  // device status bits observed by the host
   std::vector<LidarTable> tables;
-  // diagnostics: event triples (before alloc, between, after integrate)
+  // second mask / work-list / control set: with it the allocation of one
+  // sub-batch runs on `aux` while the previous sub-batch integrates
+  uint32_t* mask1;
+  uint32_t* list1;
+  unsigned int* ctl1;
+  cudaStream_t aux;
+  cudaEvent_t ev_alloc[4], ev_int[4], ev_start;
+  // diagnostics: per call (alloc start, alloc end, integrate start, integrate end)
   bool timing;
   std::vector<cudaEvent_t> events;
   size_t n_timed;
@@ -48,6 +55,7 @@ namespace {
 
 constexpr int64_t kDefaultBlocks = 1 << 18;
 constexpr size_t kTimedCalls = 4096;
+constexpr int32_t kMaxBatchFrames = 1 << 16;
 
 tsdf_status cuda_fail() {
   cudaGetLastError();
@@ -195,10 +203,21 @@ bool on_device(const tsdf_map* m) {
   return cudaGetDevice(&dev) == cudaSuccess && dev == m->device;
 }
 
-// Next free event triple when timing is enabled, else nullptr.
+// Next free event quadruple when timing is enabled, else nullptr.
 cudaEvent_t* timing_slot(tsdf_map* m) {
   if (!m->timing || m->n_timed >= kTimedCalls) return nullptr;
-  return &m->events[3 * m->n_timed++];
+  return &m->events[4 * m->n_timed++];
+}
+
+// Device view of map m using mask / list / control set `set` (0 or 1).
+MapDev view_set(const tsdf_map* m, int set) {
+  MapDev d = m->dev;
+  if (set) {
+    d.mask = m->mask1;
+    d.list = m->list1;
+    d.ctl = m->ctl1;
+  }
+  return d;
 }
 
 tsdf_status integrate_one(tsdf_map* m, int kind, const tsdf_pinhole* ph, const tsdf_lidar* li,
@@ -220,9 +239,12 @@ tsdf_status integrate_one(tsdf_map* m, int kind, const tsdf_pinhole* ph, const t
   if (ev) cudaEventRecord(ev[0], s);
   const int th = m->tile_h ? m->tile_h : pick_tile_h((int64_t)p.fr[0].width * p.fr[0].height);
   if (gbt::launch_band_alloc(p, alloc_ctas(p.fr[0], th), th, s) != cudaSuccess) return cuda_fail();
-  if (ev) cudaEventRecord(ev[1], s);
+  if (ev) {
+    cudaEventRecord(ev[1], s);
+    cudaEventRecord(ev[2], s);
+  }
   if (gbt::launch_integrate(p, m->n_ctas_integrate, s) != cudaSuccess) return cuda_fail();
-  if (ev) cudaEventRecord(ev[2], s);
+  if (ev) cudaEventRecord(ev[3], s);
   m->frames += 1;
   return TSDF_OK;
 }
@@ -237,6 +259,15 @@ tsdf_status read_counters(const tsdf_map* m, unsigned long long c[gbt::kNumCount
 }
 
 void free_map(tsdf_map* m) {
+  cudaFree(m->mask1);
+  cudaFree(m->list1);
+  cudaFree(m->ctl1);
+  if (m->aux) cudaStreamDestroy(m->aux);
+  for (int i = 0; i < 4; ++i) {
+    if (m->ev_alloc[i]) cudaEventDestroy(m->ev_alloc[i]);
+    if (m->ev_int[i]) cudaEventDestroy(m->ev_int[i]);
+  }
+  if (m->ev_start) cudaEventDestroy(m->ev_start);
   cudaFree(m->dev.keys);
   cudaFree(m->dev.vals);
   cudaFree(m->dev.mask);
@@ -309,8 +340,20 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
             cudaMalloc(&d.block_keys, sizeof(unsigned long long) * o.max_blocks) == cudaSuccess &&
             cudaMalloc(&d.counters, sizeof(unsigned long long) * gbt::kNumCounters) == cudaSuccess &&
             cudaMalloc(&d.list, sizeof(uint32_t) * o.max_blocks) == cudaSuccess &&
-            cudaMalloc(&d.ctl, sizeof(unsigned int) * 4) == cudaSuccess;
-  if (ok) ok = gbt::launch_reset(d, m->cap, 0) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+            cudaMalloc(&d.ctl, sizeof(unsigned int) * 4) == cudaSuccess &&
+            cudaMalloc(&m->mask1, sizeof(uint32_t) * cap) == cudaSuccess &&
+            cudaMalloc(&m->list1, sizeof(uint32_t) * o.max_blocks) == cudaSuccess &&
+            cudaMalloc(&m->ctl1, sizeof(unsigned int) * 4) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&m->aux, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&m->ev_start, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < 4; ++i)
+    ok = cudaEventCreateWithFlags(&m->ev_alloc[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&m->ev_int[i], cudaEventDisableTiming) == cudaSuccess;
+  if (ok)
+    ok = gbt::launch_reset(d, m->cap, 0) == cudaSuccess &&
+         cudaMemsetAsync(m->mask1, 0, sizeof(uint32_t) * cap, 0) == cudaSuccess &&
+         cudaMemsetAsync(m->ctl1, 0, sizeof(unsigned int) * 4, 0) == cudaSuccess &&
+         cudaDeviceSynchronize() == cudaSuccess;
   if (!ok) {
     free_map(m);
     return cuda_fail();
@@ -342,7 +385,7 @@ tsdf_status integrate_lidar(tsdf_map* map, const float* range_dev, const tsdf_li
 
 tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_frame_desc* frames,
                             int32_t n, void* cuda_stream) {
-  if (!maps || !frames || n_maps <= 0 || n_maps > gbt::kMaxMaps || n <= 0 || n > gbt::kMaxFrames)
+  if (!maps || !frames || n_maps <= 0 || n_maps > gbt::kMaxMaps || n <= 0 || n > kMaxBatchFrames)
     return TSDF_ERR_ARG;
   for (int i = 0; i < n_maps; ++i) {
     if (!maps[i]) return TSDF_ERR_ARG;
@@ -352,36 +395,63 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
     if (!on_device(maps[i])) return TSDF_ERR_STATE;
     if (status_from_bits(maps[i]->status_seen) != TSDF_OK) return status_from_bits(maps[i]->status_seen);
   }
-  // the params block is large; keep it off the stack
-  static thread_local BatchParams<gbt::kMaxFrames, gbt::kMaxMaps> p;
-  std::memset(&p, 0, sizeof(p));
-  p.n_frames = n;
-  p.n_maps = n_maps;
-  int ctas = 0, integ = 1;
-  for (int i = 0; i < n_maps; ++i) p.maps[i] = maps[i]->dev;
-  integ = maps[0]->n_ctas_integrate;
-  int64_t pixels = 0;
+  // every frame is checked and prepared before anything is enqueued
+  static thread_local std::vector<FrameDev> fr;
+  fr.resize(n);
   for (int f = 0; f < n; ++f) {
     const tsdf_frame_desc& fd = frames[f];
     if (fd.map < 0 || fd.map >= n_maps) return TSDF_ERR_ARG;
     tsdf_status st = fill_frame(maps[fd.map], fd.map, fd.kind, &fd.pinhole, &fd.lidar,
-                                fd.depth_dev, fd.T_world_sensor, p.fr[f]);
+                                fd.depth_dev, fd.T_world_sensor, fr[f]);
     if (st != TSDF_OK) return st;
-    p.fr[f].bit = f;
-    pixels += (int64_t)p.fr[f].width * p.fr[f].height;
   }
-  const int th = maps[0]->tile_h ? maps[0]->tile_h : pick_tile_h(pixels);
-  for (int f = 0; f < n; ++f) {
-    p.fr[f].blk_begin = ctas;
-    ctas += alloc_ctas(p.fr[f], th);
-  }
+  // the params block is large; keep it off the stack
+  static thread_local BatchParams<gbt::kMaxFrames, gbt::kMaxMaps> p;
+  tsdf_map* lead = maps[0];
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  cudaEvent_t* ev = timing_slot(maps[0]);
-  if (ev) cudaEventRecord(ev[0], s);
-  if (gbt::launch_band_alloc(p, ctas, th, s) != cudaSuccess) return cuda_fail();
-  if (ev) cudaEventRecord(ev[1], s);
-  if (gbt::launch_integrate(p, integ, s) != cudaSuccess) return cuda_fail();
-  if (ev) cudaEventRecord(ev[2], s);
+  const int n_sub = (n + gbt::kMaxFrames - 1) / gbt::kMaxFrames;
+  // Sub-batches of up to 32 frames, each one allocation launch and one
+  // integration launch.  With more than one, sub-batch b uses mask / list
+  // set b % 2 and its allocation runs on the lead map's auxiliary stream,
+  // overlapping the integration of sub-batch b - 1 on the caller's stream;
+  // it waits for the integration of b - 2, which used the same set.
+  const bool piped = n_sub > 1;
+  if (piped && (cudaEventRecord(lead->ev_start, s) != cudaSuccess ||
+                cudaStreamWaitEvent(lead->aux, lead->ev_start, 0) != cudaSuccess))
+    return cuda_fail();
+  for (int b = 0; b < n_sub; ++b) {
+    const int f0 = b * gbt::kMaxFrames, nf = std::min(gbt::kMaxFrames, n - f0);
+    std::memset(&p, 0, sizeof(p));
+    p.n_frames = nf;
+    p.n_maps = n_maps;
+    for (int i = 0; i < n_maps; ++i) p.maps[i] = view_set(maps[i], piped ? (b & 1) : 0);
+    int64_t pixels = 0;
+    for (int f = 0; f < nf; ++f) {
+      p.fr[f] = fr[f0 + f];
+      p.fr[f].bit = f;
+      pixels += (int64_t)p.fr[f].width * p.fr[f].height;
+    }
+    const int th = lead->tile_h ? lead->tile_h : pick_tile_h(pixels);
+    int ctas = 0;
+    for (int f = 0; f < nf; ++f) {
+      p.fr[f].blk_begin = ctas;
+      ctas += alloc_ctas(p.fr[f], th);
+    }
+    cudaStream_t sa = piped ? lead->aux : s;
+    if (piped && b >= 2 && cudaStreamWaitEvent(sa, lead->ev_int[(b - 2) & 3], 0) != cudaSuccess)
+      return cuda_fail();
+    cudaEvent_t* ev = timing_slot(lead);
+    if (ev) cudaEventRecord(ev[0], sa);
+    if (gbt::launch_band_alloc(p, ctas, th, sa) != cudaSuccess) return cuda_fail();
+    if (ev) cudaEventRecord(ev[1], sa);
+    if (piped && (cudaEventRecord(lead->ev_alloc[b & 3], sa) != cudaSuccess ||
+                  cudaStreamWaitEvent(s, lead->ev_alloc[b & 3], 0) != cudaSuccess))
+      return cuda_fail();
+    if (ev) cudaEventRecord(ev[2], s);
+    if (gbt::launch_integrate(p, lead->n_ctas_integrate, s) != cudaSuccess) return cuda_fail();
+    if (ev) cudaEventRecord(ev[3], s);
+    if (piped && cudaEventRecord(lead->ev_int[b & 3], s) != cudaSuccess) return cuda_fail();
+  }
   for (int f = 0; f < n; ++f) maps[frames[f].map]->frames += 1;
   return TSDF_OK;
 }
@@ -432,7 +502,7 @@ tsdf_status map_stats(const tsdf_map* map, int64_t out[8]) {
 tsdf_status map_timing(tsdf_map* map, int32_t enable) {
   if (!map) return TSDF_ERR_ARG;
   if (enable && map->events.empty()) {
-    map->events.resize(3 * kTimedCalls);
+    map->events.resize(4 * kTimedCalls);
     for (cudaEvent_t& e : map->events)
       if (cudaEventCreate(&e) != cudaSuccess) return cuda_fail();
   }
@@ -445,10 +515,11 @@ tsdf_status map_kernel_times(tsdf_map* map, double out_ms[2], int64_t* calls) {
   if (!map || !out_ms || !calls) return TSDF_ERR_ARG;
   out_ms[0] = out_ms[1] = 0.0;
   for (size_t i = 0; i < map->n_timed; ++i) {
-    cudaEvent_t* e = &map->events[3 * i];
+    cudaEvent_t* e = &map->events[4 * i];
     float a = 0.0f, b = 0.0f;
-    if (cudaEventSynchronize(e[2]) != cudaSuccess || cudaEventElapsedTime(&a, e[0], e[1]) != cudaSuccess ||
-        cudaEventElapsedTime(&b, e[1], e[2]) != cudaSuccess)
+    if (cudaEventSynchronize(e[3]) != cudaSuccess || cudaEventSynchronize(e[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&a, e[0], e[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&b, e[2], e[3]) != cudaSuccess)
       return cuda_fail();
     out_ms[0] += a;
     out_ms[1] += b;
@@ -511,7 +582,11 @@ tsdf_status map_export(const tsdf_map* map, int32_t* keys_host, float* dist_host
 tsdf_status map_reset(tsdf_map* map, void* cuda_stream) {
   if (!map) return TSDF_ERR_ARG;
   if (!on_device(map)) return TSDF_ERR_STATE;
-  if (gbt::launch_reset(map->dev, map->cap, (cudaStream_t)cuda_stream) != cudaSuccess) return cuda_fail();
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (gbt::launch_reset(map->dev, map->cap, s) != cudaSuccess ||
+      cudaMemsetAsync(map->mask1, 0, sizeof(uint32_t) * map->cap, s) != cudaSuccess ||
+      cudaMemsetAsync(map->ctl1, 0, sizeof(unsigned int) * 4, s) != cudaSuccess)
+    return cuda_fail();
   map->status_seen = 0;
   map->frames = 0;
   return TSDF_OK;

@@ -53,6 +53,16 @@ def test_room_300_frames_fp32(room):
     _record("room300_fp32", {**st, "max_err_vox": st["max_err"] / v, "rms_err_vox": st["rms_err"] / v})
 
 
+def test_room_300_frames_one_call_pipelined(room):
+    """All 300 frames in one integrate_batch call (ten pipelined sub-batches)."""
+    w, orc, oc = room
+    gpu, gs, status = run_gpu(w.frames, w.voxel_size, batch=300)
+    assert status == 0 and gs["launches"] == 10
+    st = compare(gpu, orc, 1e-4 * float(np.float32(w.voxel_size)), "room300_fp32_pipelined")
+    assert gs["voxel_updates"] == oc["total_updates"]
+    _record("room300_fp32_pipelined", st)
+
+
 def test_room_300_frames_fp16(room):
     w, orc, oc = room
     gpu, gs, status = run_gpu(w.frames, w.voxel_size, storage=1, batch=BATCH)

@@ -146,6 +146,22 @@ def test_batched_equals_sequential_and_oracle():
     _record("batched8", compare(bat, orc, tol_pinhole(w.voxel_size), "batched8"))
 
 
+def test_pipelined_batch_equals_sequential():
+    """One integrate_batch call with 70 frames: three sub-batches whose
+    allocations overlap the previous sub-batch's integration on a second
+    stream (alternating mask / list sets); the map equals one frame per
+    launch bit for bit."""
+    w = synth.config_room(n_frames=300)
+    frames = w.frames[100:170]
+    seq, _, _ = run_gpu(frames, w.voxel_size)
+    pip, stats, st = run_gpu(frames, w.voxel_size, batch=70)
+    assert st == 0 and stats["launches"] == 3
+    for a, b in zip(seq, pip):
+        np.testing.assert_array_equal(a, b)
+    orc, _ = run_oracle(frames, w.voxel_size)
+    _record("pipelined70", compare(pip, orc, tol_pinhole(w.voxel_size), "pipelined70"))
+
+
 def test_multi_map_batch():
     """One launch over three maps with different voxel sizes and interleaved
     frames: each map equals its own one-frame-per-launch result."""
