@@ -219,12 +219,11 @@ __device__ __forceinline__ bool pixel_segment(const FrameDev& F, const MapDev& m
   return valid;
 }
 
-// One CTA per kTileW x kTileH pixel tile of one frame.  Each warp walks the
-// band segments of one pixel row at a time; a lane whose left neighbour is
-// in the same block at the same step leaves that block to it, the others
-// record their block in a CTA-local set; then the tile's distinct blocks are
-// claimed in the global hash.  Segments that start far from the sensor's
-// block take a slower path with full keys and direct global claims.
+// One CTA per kTileW x TH pixel tile of one frame.  Each warp walks the
+// band segments of one pixel row at a time and records the blocks met in a
+// CTA-local set; then the tile's distinct blocks are claimed in the global
+// hash.  Segments that start far from the sensor's block count cells from
+// their own start cell and claim their blocks directly.
 template <int NF, int NM, int TH>
 __global__ void __launch_bounds__(kAllocThreads)
     band_alloc_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
@@ -236,10 +235,17 @@ __global__ void __launch_bounds__(kAllocThreads)
   __shared__ float s_ray[kTileW + TH];  // pinhole: (i - cu) / fu per column, (j - cv) / fv per row
   for (int i = threadIdx.x; i < kSetSize; i += kAllocThreads) s_set[i] = kEmptyRel;
   if (threadIdx.x == 0) s_nkeys = 0;
+  // frame of this CTA: the last frame whose first tile is <= blockIdx.x
   int f = 0;
-#pragma unroll 1
-  for (int k = 1; k < p.n_frames; ++k)
-    if ((int)blockIdx.x >= p.fr[k].blk_begin) f = k;
+  for (int lo = 1, hi = p.n_frames - 1; lo <= hi;) {
+    const int mid = (lo + hi) >> 1;
+    if ((int)blockIdx.x >= p.fr[mid].blk_begin) {
+      f = mid;
+      lo = mid + 1;
+    } else {
+      hi = mid - 1;
+    }
+  }
   const FrameDev& F = p.fr[f];
   const MapDev& m = p.maps[F.map];
   const int tiles_x = (F.width + kTileW - 1) / kTileW;
@@ -287,16 +293,13 @@ __global__ void __launch_bounds__(kAllocThreads)
     }
     segs += live ? 1u : 0u;
     while (__any_sync(0xffffffffu, live)) {
-      const uint32_t left = __shfl_up_sync(0xffffffffu, wk.key, 1);
       if (live) {
         ++cells;
-        if (wk.key & kFarFlag) {
+        if (wk.key & kFarFlag)
           claim_block(m, rel_to_key(wk.key & ~kFarFlag, F.a, b0x, b0y, b0z), F.bit);
-        } else if (!(lane > 0 && left == wk.key) && !set_insert(s_set, wk.key)) {
+        else if (!set_insert(s_set, wk.key))
           claim_block(m, rel_to_key(wk.key, F.a), F.bit);
-        }
         live = wk.next();
-        if (!live) wk.key = kEmptyRel;
       }
     }
   }
