@@ -126,6 +126,24 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def reduce_max(x: float, ws: int, device: str = "cuda") -> float:
+    """Max of a per-rank scalar over all ranks (the job's time is its slowest
+    rank's); the identity for a single process."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(work_per_rank: float, ms_max: float, ws: int) -> float:
+    """Whole-job throughput of `ws` replicas each doing `work_per_rank` units,
+    timed by the slowest rank."""
+    return ws * work_per_rank / (ms_max * 1e-3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -266,13 +284,7 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1) / k
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return reduce_max(e0.elapsed_time(e1) / k, ws)
 
     # ---- headline: FP32 storage, batched launches
     m = gt.TsdfMap(w.voxel_size, w.truncation_voxels, w.max_weight, storage=gt.STORAGE_FP32)
@@ -307,8 +319,8 @@ def main():
     alloc_ops_per_launch = (OPS_PER_SEGMENT * st["segments"] + OPS_PER_CELL * st["cells"]) / launches_per_step
     alloc_achieved = alloc_ops_per_launch / (alloc_ms_per_launch * 1e-3)
     alloc_share = alloc_ms / max(alloc_ms + integ_ms, 1e-9)
-    value = ws * updates_per_step / (ms * 1e-3)
-    fps = ws * n_frames / (ms * 1e-3)
+    value = aggregate_rate(updates_per_step, ms, ws)
+    fps = aggregate_rate(n_frames, ms, ws)
 
     # ---- end to end through the public API with host buffers
     e2e_step_inner = make_step(m, args.batch)
@@ -328,12 +340,7 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / k_e2e
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = reduce_max((time.perf_counter() - t0) * 1e3 / k_e2e, ws)
 
     forms = {}
     if not args.no_forms:
@@ -430,12 +437,7 @@ def _setup_device():
 
 
 def _max_over_ranks(torch, ws, x):
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([x], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-    return x
+    return reduce_max(x, ws)
 
 
 def bench_rig(args):
