@@ -48,6 +48,7 @@ def _load():
             lib.orc_create.restype = P
             lib.orc_destroy.argtypes = [P]
             lib.orc_set_lidar_sampling.argtypes = [P, I, F]
+            lib.orc_set_occupancy.argtypes = [P, F, F]
             lib.orc_integrate_pinhole.argtypes = [P, P, I, I, F, F, F, F, P]
             lib.orc_integrate_pinhole.restype = I
             lib.orc_integrate_lidar.argtypes = [P, P, I, I, F, F, F, F, F, P]
@@ -95,6 +96,10 @@ class OracleMap:
 
     def set_lidar_sampling(self, nearest: bool = False, guard: float = 0.0):
         self._lib.orc_set_lidar_sampling(self._h, int(nearest), guard)
+
+    def set_occupancy(self, l_occ: float, l_free: float):
+        """Occupancy layer: D becomes the log-odds, W the number of updates."""
+        self._lib.orc_set_occupancy(self._h, l_occ, l_free)
 
     def integrate(self, sensor: dict, T: np.ndarray, depth: np.ndarray):
         depth = np.ascontiguousarray(depth, np.float32)

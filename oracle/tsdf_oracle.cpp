@@ -16,7 +16,10 @@
  *     is sampled (nearest pixel for a camera, guarded bilinear for LiDAR),
  *     d_p = d - d_v is formed, voxels with d_p < -tau are skipped, d_p is
  *     clamped to +tau, and the weighted running average with constant weight
- *     1 is applied, weights added up to max_weight (Sec. IV-B).
+ *     1 is applied, weights added up to max_weight (Sec. IV-B);
+ *   - occupancy layer (Sec. IV-B, second functor), optional: the same voxels
+ *     instead add a constant log-odds, negative in front of the surface
+ *     (d_p > 0), positive otherwise.
  *
  * Storage: std::unordered_map from integer block coordinates to a block of
  * 8x8x8 voxels holding D (double) and W (double), voxel index
@@ -101,6 +104,10 @@ struct Oracle {
   float tauf;
   int lidar_nearest = 0;
   float guard_f;  // LiDAR fg/bg guard threshold (metres)
+  // occupancy layer (Sec. IV-B, second functor): D holds the log-odds, W
+  // the number of updates
+  int occupancy = 0;
+  double l_occ = 0.0, l_free = 0.0;
   std::unordered_map<Key, std::unique_ptr<Block>, KeyHash> blocks;
   Counters last;
   int64_t total_updates = 0;
@@ -250,6 +257,15 @@ inline void tsdf_update(double& D, double& W, double s, double wmax) {
   W = std::min(W + w, wmax);
 }
 
+/* Occupancy functor (Sec. IV-B): running addition of a constant negative
+ * log-odds where the voxel lies in front of the measured surface (d_p > 0)
+ * and a constant positive one otherwise (-tau <= d_p <= 0; the voxels more
+ * than tau behind it were skipped as unobserved). */
+inline void occupancy_update(double& L, double& N, bool in_front, double l_occ, double l_free) {
+  L += in_front ? l_free : l_occ;
+  N += 1.0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -268,6 +284,16 @@ void* orc_create(float voxel_size, int32_t truncation_voxels, float max_weight) 
 }
 
 void orc_destroy(void* h) { delete static_cast<Oracle*>(h); }
+
+/* Occupancy layer: voxels accumulate log-odds l_occ (on or behind the
+ * surface, within tau) or l_free (in front of it) instead of the TSDF; the
+ * exported D is the log-odds and W the number of updates. */
+void orc_set_occupancy(void* h, float l_occ, float l_free) {
+  auto* m = static_cast<Oracle*>(h);
+  m->occupancy = 1;
+  m->l_occ = (double)l_occ;
+  m->l_free = (double)l_free;
+}
 
 /* LiDAR sampling: nearest != 0 selects nearest-cell sampling (a test mode);
  * guard is the fg/bg threshold of the bilinear mode in metres (<= 0: tau). */
@@ -358,8 +384,12 @@ int32_t orc_integrate_pinhole(void* h, const float* depth, int32_t W, int32_t H,
                                 ((double)g[2] + 0.5) * m.vd};
           double pC[3];
           to_sensor64(P, pL, pC);
-          const double s = std::min((double)d - pC[2], m.taud);
-          tsdf_update(blk->D[l], blk->W[l], s, (double)m.wmax);
+          if (m.occupancy) {
+            occupancy_update(blk->D[l], blk->W[l], d - p[2] > 0.0f, m.l_occ, m.l_free);
+          } else {
+            const double s = std::min((double)d - pC[2], m.taud);
+            tsdf_update(blk->D[l], blk->W[l], s, (double)m.wmax);
+          }
           ++updated;
         }
   }
@@ -497,8 +527,12 @@ int32_t orc_integrate_lidar(void* h, const float* range, int32_t n_az, int32_t n
           double pC[3];
           to_sensor64(P, pL, pC);
           const double r64 = std::sqrt(pC[0] * pC[0] + pC[1] * pC[1] + pC[2] * pC[2]);
-          const double s = std::min(dsamp64 - r64, m.taud);
-          tsdf_update(blk->D[l], blk->W[l], s, (double)m.wmax);
+          if (m.occupancy) {
+            occupancy_update(blk->D[l], blk->W[l], dsamp32 - r > 0.0f, m.l_occ, m.l_free);
+          } else {
+            const double s = std::min(dsamp64 - r64, m.taud);
+            tsdf_update(blk->D[l], blk->W[l], s, (double)m.wmax);
+          }
           ++updated;
         }
   }

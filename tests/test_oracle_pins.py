@@ -413,3 +413,67 @@ def test_lidar_brute_force_outdoor():
     # its error, below 1e-4 px at these image sizes, times the largest spread
     # the guard lets through (tau) bounds the difference to FP64 bilinear.
     _check_lidar_single(lid, T, img, keys, D, W, v, tau, tau, tol=1e-4 * tau)
+
+
+# ------------------------------------------------------- occupancy layer
+
+L_OCC, L_FREE = F32(0.85), F32(-0.4)
+
+
+def test_occupancy_plane_closed_form():
+    """Occupancy functor (Sec. IV-B): 7 frames of the plane z = 2 m then 5 at
+    z = 2.12 m; a voxel in view adds l_free per frame that sees it in front
+    of the surface (d_p > 0) and l_occ per frame that sees it within tau
+    behind (-tau <= d_p <= 0); voxels further behind are never updated."""
+    cam = synth.pinhole(64, 48, 50.0, 32.0, 24.0)
+    T = np.eye(4)
+    imgs = [synth.render_pinhole(scene(prim(PLANE, 0, 0, 1, z)), T, cam["fu"], cam["fv"],
+                                 cam["cu"], cam["cv"], 64, 48) for z in (2.0, 2.12)]
+    m = oracle.OracleMap(0.05)
+    m.set_occupancy(L_OCC, L_FREE)
+    for img in [imgs[0]] * 7 + [imgs[1]] * 5:
+        m.integrate(cam, T, img)
+    keys, L, N = m.export()
+    v = F32(0.05)
+    tau = _tau(v)
+    pC = G.to_sensor(T, G.voxel_centres(keys, v))
+    _, _, inside, ok = G.pinhole_pixel(cam, pC, 1e-3)
+    z = pC[..., 2]
+    exp_L = np.zeros_like(z)
+    exp_N = np.zeros_like(z)
+    for zs, k in ((float(np.float32(2.0)), 7), (float(np.float32(2.12)), 5)):
+        dp = zs - z
+        ok &= (np.abs(dp) > 1e-5) & (np.abs(dp + tau) > 1e-5)
+        seen = inside & (dp >= -tau)
+        exp_L += np.where(seen, k * np.where(dp > 0, L_FREE, L_OCC), 0.0)
+        exp_N += np.where(seen, k, 0)
+    assert ok.sum() > 0.9 * ok.size
+    np.testing.assert_array_equal(N[ok], exp_N[ok])
+    np.testing.assert_allclose(L[ok], exp_L[ok], rtol=0, atol=1e-12)
+    # both signs and the mixed case occur
+    assert (exp_L[ok] > 0).any() and (exp_L[ok] < 0).any()
+    mixed = ok & (exp_N == 12) & (np.abs(exp_L - (7 * L_OCC + 5 * L_FREE)) < 1e-9)
+    assert mixed.sum() > 0
+
+
+def test_occupancy_lidar_sphere():
+    """Inside a sphere of radius 10 m: voxels with |p| < 10 are free, those
+    within tau outside it occupied, one observation each."""
+    lid = synth.lidar64(n_az=128, n_el=16)
+    T = _lidar_pose(3)
+    img = np.full((16, 128), 10.0, np.float32)
+    m = oracle.OracleMap(0.05)
+    m.set_occupancy(L_OCC, L_FREE)
+    m.integrate(lid, T, img)
+    keys, L, N = m.export()
+    v = F32(0.05)
+    tau = _tau(v)
+    pC = G.to_sensor(T, G.voxel_centres(keys, v))
+    u, vv, r = G.lidar_coords(lid, pC)
+    d, valid, ok = G.lidar_bilinear(lid, img, u, vv, tau)
+    dp = d - r
+    ok &= (np.abs(dp) > 1e-5) & (np.abs(dp + tau) > 1e-5)
+    seen = valid & (dp >= -tau)
+    np.testing.assert_array_equal(N[ok], seen[ok].astype(float))
+    np.testing.assert_allclose(L[ok], np.where(seen, np.where(dp > 0, L_FREE, L_OCC), 0)[ok],
+                               rtol=0, atol=1e-12)
