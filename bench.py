@@ -375,6 +375,17 @@ def main():
             "ms_per_step": ms2, "voxel_updates_per_s": ws * updates_per_step / (ms2 * 1e-3),
             "frames_per_s": ws * n_frames / (ms2 * 1e-3)}
         m2.close()
+        # occupancy layer (second update functor) over the same frames
+        m3 = gt.TsdfMap(w.voxel_size, w.truncation_voxels, w.max_weight,
+                        layer=gt.LAYER_OCCUPANCY)
+        s3 = make_step(m3, args.batch)
+        for _ in range(args.warmup):
+            s3()
+        ms3 = timed(s3, args.steps)
+        forms[f"occupancy_batched_{args.batch}"] = {
+            "ms_per_step": ms3, "voxel_updates_per_s": ws * m3.stats()["voxel_updates"] / (ms3 * 1e-3),
+            "frames_per_s": ws * n_frames / (ms3 * 1e-3)}
+        m3.close()
         forms["fp32_batched_speedup_vs_one_frame"] = ms1 / ms
         forms["fp16_batched_speedup_vs_one_frame"] = ms1 / ms2
 

@@ -75,6 +75,13 @@ typedef struct {
 } tsdf_lidar;
 
 enum { TSDF_STORAGE_FP32 = 0, TSDF_STORAGE_FP16 = 1 };
+/* Layers (Sec. IV-A: a map of co-located layers; Sec. IV-B: one update
+ * functor per layer).  An occupancy layer holds one FP32 log-odds per voxel:
+ * every voxel that passes the same projection test as the TSDF (d_p >= -tau)
+ * adds l_free if it lies in front of the surface (d_p > 0) and l_occ
+ * otherwise; `storage` is ignored, exported distances are the log-odds and
+ * exported / queried weights are 0. */
+enum { TSDF_LAYER_TSDF = 0, TSDF_LAYER_OCCUPANCY = 1 };
 enum { TSDF_SENSOR_PINHOLE = 0, TSDF_SENSOR_LIDAR = 1 };
 
 /* Map options.  max_blocks: pool size in blocks (4 KiB per block in FP32,
@@ -86,7 +93,9 @@ enum { TSDF_SENSOR_PINHOLE = 0, TSDF_SENSOR_LIDAR = 1 };
  * depend on them): alloc_tile_h is the pixel-tile height of the allocation
  * kernel, 16 or 32 (0 = chosen from the pixels per launch);
  * integrate_ctas_per_sm is the integration kernel's resident CTAs per SM
- * (0 = as many as fit).  For integrate_batch the first map's knobs apply. */
+ * (0 = as many as fit).  For integrate_batch the first map's knobs apply.
+ * layer selects the update functor (all maps of one integrate_batch call
+ * must share layer and storage). */
 typedef struct {
   int32_t storage;
   int64_t max_blocks;
@@ -95,6 +104,8 @@ typedef struct {
   float lidar_guard;
   int32_t alloc_tile_h;
   int32_t integrate_ctas_per_sm;
+  int32_t layer;       /* TSDF_LAYER_TSDF or TSDF_LAYER_OCCUPANCY */
+  float l_occ, l_free; /* occupancy: log-odds added per update (0, 0: 0.85, -0.4) */
 } tsdf_map_opts;
 
 /* One frame of a batch.  `map` indexes the maps array of integrate_batch;

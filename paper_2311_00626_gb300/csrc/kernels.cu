@@ -418,6 +418,18 @@ __device__ __forceinline__ void fuse(float& D, float& W, float s, float wmax) {
   W = fminf(wn, wmax);
 }
 
+// Update functor of a voxel that passed the projection test, d_p >= -tau:
+// the TSDF average, or for an occupancy layer (Sec. IV-B, second functor)
+// the running addition of l_free in front of the surface (d_p > 0) and
+// l_occ otherwise.
+template <int STORAGE>
+__device__ __forceinline__ void apply(const MapDev& m, float& D, float& W, float dp) {
+  if (STORAGE == kStorageOcc)
+    D += dp > 0.0f ? m.l_free : m.l_occ;
+  else
+    fuse(D, W, fminf(dp, m.tau), m.wmax);
+}
+
 template <int STORAGE>
 struct Voxels4;
 
@@ -434,6 +446,19 @@ struct Voxels4<kStorageF32> {
     float4* dst = reinterpret_cast<float4*>(m.pool) + (size_t)pool * 256 + 2 * t;
     dst[0] = make_float4(D[0], W[0], D[1], W[1]);
     dst[1] = make_float4(D[2], W[2], D[3], W[3]);
+  }
+};
+
+template <>
+struct Voxels4<kStorageOcc> {
+  __device__ __forceinline__ static void load(const MapDev& m, int pool, int t, float* D, float* W) {
+    const float4 a = reinterpret_cast<const float4*>(m.pool)[(size_t)pool * 128 + t];
+    D[0] = a.x; D[1] = a.y; D[2] = a.z; D[3] = a.w;
+    W[0] = W[1] = W[2] = W[3] = 0.0f;
+  }
+  __device__ __forceinline__ static void store(const MapDev& m, int pool, int t, const float* D,
+                                               const float* W) {
+    reinterpret_cast<float4*>(m.pool)[(size_t)pool * 128 + t] = make_float4(D[0], D[1], D[2], D[3]);
   }
 };
 
@@ -492,7 +517,7 @@ __device__ __forceinline__ void row_points(const FrameDev& F, float v, const Vox
 // into every frame (Eq. 2, nearest pixel) and issues all depth loads, phase 2
 // applies the updates in frame order.  An out-of-image projection reads no
 // pixel and yields d = 0, which is invalid like a missing depth.
-template <int NQ, class P>
+template <int NQ, int STORAGE, class P>
 __device__ __forceinline__ void fuse_pinhole(const P& p, const int (&fq)[4], const MapDev& m,
                                              const VoxelRow& r, float* D, float* W,
                                              unsigned long long& upd) {
@@ -518,13 +543,14 @@ __device__ __forceinline__ void fuse_pinhole(const P& p, const int (&fq)[4], con
     for (int i = 0; i < 4; ++i) {
       const float dp = __fsub_rn(d[q][i], z[q][i]);
       if (d[q][i] > 0.0f && d[q][i] <= FLT_MAX && !(dp < -m.tau)) {
-        fuse(D[i], W[i], fminf(dp, m.tau), m.wmax);
+        apply<STORAGE>(m, D[i], W[i], dp);
         ++upd;
       }
     }
 }
 
 // One frame of any sensor kind, voxel by voxel.
+template <int STORAGE>
 __device__ __forceinline__ void fuse_any(const FrameDev& F, const MapDev& m, const VoxelRow& r,
                                          float* D, float* W, unsigned long long& upd) {
   float px[4], py[4], pz[4];
@@ -535,7 +561,7 @@ __device__ __forceinline__ void fuse_any(const FrameDev& F, const MapDev& m, con
     if (!sample(F, m, px[i], py[i], pz[i], d, dv)) continue;
     const float dp = __fsub_rn(d, dv);
     if (dp < -m.tau) continue;
-    fuse(D[i], W[i], fminf(dp, m.tau), m.wmax);
+    apply<STORAGE>(m, D[i], W[i], dp);
     ++upd;
   }
 }
@@ -614,17 +640,17 @@ __global__ void __launch_bounds__(kIntegrateThreads)
             }
           }
         }
-        if (nq == 4) fuse_pinhole<4>(p, fq, m, vr, D, W, my_upd);
+        if (nq == 4) fuse_pinhole<4, STORAGE>(p, fq, m, vr, D, W, my_upd);
         else if (nq >= 1) {
           for (int q = 0; q < nq; ++q) {
             const int fq1[4] = {fq[q], -1, -1, -1};
-            fuse_pinhole<1>(p, fq1, m, vr, D, W, my_upd);
+            fuse_pinhole<1, STORAGE>(p, fq1, m, vr, D, W, my_upd);
           }
         }
         else {
           const int f = __ffs(bits) - 1;  // a LiDAR frame
           bits &= bits - 1u;
-          fuse_any(p.fr[f], m, vr, D, W, my_upd);
+          fuse_any<STORAGE>(p.fr[f], m, vr, D, W, my_upd);
         }
       }
       Voxels4<STORAGE>::store(m, pool, t, D, W);
@@ -672,7 +698,9 @@ __global__ void query_kernel(const MapDev m, const float* __restrict__ pts, int6
       const int val = m.vals[slot];
       if (val >= 0) {
         const int l = (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7);
-        if (STORAGE == kStorageF32) {
+        if (STORAGE == kStorageOcc) {
+          outD = reinterpret_cast<const float*>(m.pool)[(size_t)val * 512 + l];
+        } else if (STORAGE == kStorageF32) {
           const float2 v = reinterpret_cast<const float2*>(m.pool)[(size_t)val * 512 + l];
           outD = v.x;
           outW = v.y;
@@ -713,7 +741,9 @@ cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile
 template <int NF, int NM>
 cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStream_t s) {
   // all maps of a batch share one storage type (checked by the host API)
-  if (p.maps[0].storage == kStorageF16)
+  if (p.maps[0].storage == kStorageOcc)
+    integrate_kernel<NF, NM, kStorageOcc><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+  else if (p.maps[0].storage == kStorageF16)
     integrate_kernel<NF, NM, kStorageF16><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
   else
     integrate_kernel<NF, NM, kStorageF32><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
@@ -732,7 +762,9 @@ cudaError_t launch_query(const MapDev& m, const float* pts, int64_t n, float* di
   if (n <= 0) return cudaSuccess;
   const int threads = 256;
   const unsigned blocks = (unsigned)((n + threads - 1) / threads);
-  if (m.storage == kStorageF16)
+  if (m.storage == kStorageOcc)
+    query_kernel<kStorageOcc><<<blocks, threads, 0, s>>>(m, pts, n, dist, weight);
+  else if (m.storage == kStorageF16)
     query_kernel<kStorageF16><<<blocks, threads, 0, s>>>(m, pts, n, dist, weight);
   else
     query_kernel<kStorageF32><<<blocks, threads, 0, s>>>(m, pts, n, dist, weight);
@@ -750,7 +782,10 @@ cudaError_t launch_reset(const MapDev& m, uint32_t cap, cudaStream_t s) {
 int integrate_ctas_per_sm(int storage) {
   int n = 0;
   cudaError_t e;
-  if (storage == kStorageF16)
+  if (storage == kStorageOcc)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageOcc>, kIntegrateThreads, 0);
+  else if (storage == kStorageF16)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageF16>, kIntegrateThreads, 0);
   else

@@ -290,12 +290,23 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   if (!out || !(voxel_size > 0.0f) || !std::isfinite(voxel_size) || truncation_voxels <= 0 ||
       !(max_weight > 0.0f) || !std::isfinite(max_weight))
     return TSDF_ERR_ARG;
-  tsdf_map_opts o{TSDF_STORAGE_FP32, kDefaultBlocks, 0, 0, 0.0f, 0, 0};
+  tsdf_map_opts o{TSDF_STORAGE_FP32, kDefaultBlocks, 0, 0, 0.0f, 0, 0, TSDF_LAYER_TSDF, 0.0f, 0.0f};
   if (opts) o = *opts;
+  if (o.layer != TSDF_LAYER_TSDF && o.layer != TSDF_LAYER_OCCUPANCY) return TSDF_ERR_ARG;
+  if (!std::isfinite(o.l_occ) || !std::isfinite(o.l_free)) return TSDF_ERR_ARG;
+  if (o.layer == TSDF_LAYER_OCCUPANCY) {
+    o.storage = gbt::kStorageOcc;
+    if (o.l_occ == 0.0f && o.l_free == 0.0f) {
+      o.l_occ = 0.85f;
+      o.l_free = -0.4f;
+    }
+  }
   if (o.alloc_tile_h != 0 && o.alloc_tile_h != gbt::kTileHSmall && o.alloc_tile_h != gbt::kTileHBig)
     return TSDF_ERR_ARG;
   if (o.integrate_ctas_per_sm < 0) return TSDF_ERR_ARG;
-  if (o.storage != TSDF_STORAGE_FP32 && o.storage != TSDF_STORAGE_FP16) return TSDF_ERR_ARG;
+  if (o.storage != TSDF_STORAGE_FP32 && o.storage != TSDF_STORAGE_FP16 &&
+      o.storage != gbt::kStorageOcc)
+    return TSDF_ERR_ARG;
   if (o.max_blocks <= 0) o.max_blocks = kDefaultBlocks;
   if (o.max_blocks > (1ll << 27)) return TSDF_ERR_ARG;
   int64_t cap = 1;
@@ -332,7 +343,9 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   d.inv_tau = 1.0f / d.tau;
   d.wmax = max_weight;
   d.guard = o.lidar_guard > 0.0f ? o.lidar_guard : d.tau;
-  const size_t voxel_bytes = o.storage == TSDF_STORAGE_FP16 ? 4 : 8;
+  d.l_occ = o.l_occ;
+  d.l_free = o.l_free;
+  const size_t voxel_bytes = o.storage == TSDF_STORAGE_FP32 ? 8 : 4;
   bool ok = cudaMalloc(&d.keys, sizeof(unsigned long long) * cap) == cudaSuccess &&
             cudaMalloc(&d.vals, sizeof(int32_t) * cap) == cudaSuccess &&
             cudaMalloc(&d.mask, sizeof(uint32_t) * cap) == cudaSuccess &&
@@ -541,7 +554,7 @@ tsdf_status map_export(const tsdf_map* map, int32_t* keys_host, float* dist_host
   if (cudaMemcpy(bk.data(), map->dev.block_keys, sizeof(unsigned long long) * nb,
                  cudaMemcpyDeviceToHost) != cudaSuccess)
     return cuda_fail();
-  const size_t voxel_bytes = map->storage == TSDF_STORAGE_FP16 ? 4 : 8;
+  const size_t voxel_bytes = map->storage == TSDF_STORAGE_FP32 ? 8 : 4;
   std::vector<unsigned char> pool;
   if (dist_host || weight_host) {
     pool.resize(voxel_bytes * gbt::kBlockVoxels * nb);
@@ -563,7 +576,10 @@ tsdf_status map_export(const tsdf_map* map, int32_t* keys_host, float* dist_host
     if (pool.empty()) continue;
     for (int l = 0; l < gbt::kBlockVoxels; ++l) {
       float D, W;
-      if (map->storage == TSDF_STORAGE_FP16) {
+      if (map->storage == gbt::kStorageOcc) {
+        D = reinterpret_cast<const float*>(pool.data())[(size_t)i * 512 + l];
+        W = 0.0f;
+      } else if (map->storage == TSDF_STORAGE_FP16) {
         const __half2 h = reinterpret_cast<const __half2*>(pool.data())[(size_t)i * 512 + l];
         D = __low2float(h) * tau;
         W = __high2float(h);

@@ -40,7 +40,9 @@ enum : int {
 enum : unsigned long long { kStPoolFull = 1, kStHashFull = 2, kStListFull = 4, kStTimeout = 8 };
 
 enum : int { kSensorPinhole = 0, kSensorLidar = 1 };
-enum : int { kStorageF32 = 0, kStorageF16 = 1 };
+// Voxel storage: TSDF {D, W} as FP32 or FP16 (D / tau), or occupancy
+// log-odds as one FP32 value.
+enum : int { kStorageF32 = 0, kStorageF16 = 1, kStorageOcc = 2 };
 
 // Device view of one map.  The work list holds the hash slots met by the
 // frames of the batch in flight; the integration launch consumes it and its
@@ -69,6 +71,7 @@ struct MapDev {
   float inv_tau;
   float wmax;
   float guard;                    // LiDAR bilinear guard (m)
+  float l_occ, l_free;            // occupancy layer: log-odds added per update
 };
 
 // One frame as the kernels see it.  Geometry is anchor-relative: a is the

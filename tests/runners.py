@@ -4,11 +4,14 @@ from __future__ import annotations
 import numpy as np
 
 
-def run_oracle(frames, voxel_size, trunc=4, wmax=100.0, lidar_nearest=False, guard=0.0):
+def run_oracle(frames, voxel_size, trunc=4, wmax=100.0, lidar_nearest=False, guard=0.0,
+               occupancy=None):
     import oracle
     m = oracle.OracleMap(voxel_size, trunc, wmax)
     if lidar_nearest or guard:
         m.set_lidar_sampling(lidar_nearest, guard)
+    if occupancy is not None:
+        m.set_occupancy(*occupancy)
     cells = 0
     for f in frames:
         m.integrate(f.sensor, f.T, f.depth)
@@ -26,13 +29,15 @@ def to_device(frames):
 
 
 def run_gpu(frames, voxel_size, trunc=4, wmax=100.0, storage=0, batch=1, lidar_nearest=False,
-            guard=0.0, max_blocks=0, keep=False):
+            guard=0.0, max_blocks=0, keep=False, occupancy=None):
     """Integrate `frames` (in order) into a fresh map, `batch` frames per
     integrate_batch call (batch=1: integrate_depth / integrate_lidar)."""
     import torch
     import paper_2311_00626_gb300 as gt
+    occ = {} if occupancy is None else {"layer": gt.LAYER_OCCUPANCY, "l_occ": occupancy[0],
+                                        "l_free": occupancy[1]}
     m = gt.TsdfMap(voxel_size, trunc, wmax, storage=storage, max_blocks=max_blocks,
-                   lidar_nearest=lidar_nearest, lidar_guard=guard)
+                   lidar_nearest=lidar_nearest, lidar_guard=guard, **occ)
     dev = to_device(frames)
     if batch == 1:
         for f, d in zip(frames, dev):
@@ -67,3 +72,17 @@ def compare(gpu, orc, tol_d, label=""):
     assert np.all(gD[~obs] == 0)
     return {"blocks": len(gk), "observed": int(obs.sum()), "max_err": float(err.max()),
             "rms_err": float(np.sqrt(np.mean(err ** 2)))}
+
+
+def compare_occupancy(gpu, orc, n_frames, l_max, label=""):
+    """Block set bit-exact; log-odds within the FP32 error of a running sum
+    of n_frames terms of magnitude <= l_max (n * ulp(n * l_max) / 2)."""
+    gk, gL, _ = gpu
+    ok, oL, oN = orc
+    np.testing.assert_array_equal(gk, ok, err_msg=f"{label}: block sets differ")
+    tol = n_frames * float(np.spacing(np.float32(n_frames * l_max))) / 2 + 1e-12
+    err = np.abs(gL.astype(np.float64) - oL)
+    assert err.max() <= tol, f"{label}: max |dL| {err.max():.3e} > {tol:.3e}"
+    assert np.all(gL[oN == 0] == 0)
+    return {"blocks": len(gk), "observed": int((oN > 0).sum()), "max_err": float(err.max()),
+            "tol": tol}

@@ -16,7 +16,7 @@ import pytest
 
 import synth
 from synth.configs import Frame
-from tests.runners import compare, run_gpu, run_oracle
+from tests.runners import compare, compare_occupancy, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -334,3 +334,42 @@ def test_far_segments_small_voxels():
     tol = tol_pinhole(0.0005) + 2 * float(np.spacing(np.float32(2.0)))
     st = _parity("far_small_voxels", w.frames, 0.0005, tol)
     assert st["blocks"] > 1000
+
+
+# --------------------------------------------------------------- occupancy
+
+OCC = (float(np.float32(0.85)), float(np.float32(-0.4)))
+
+
+def _occ_parity(name, frames, v, batch=1):
+    orc, oc = run_oracle(frames, v, occupancy=OCC)
+    gpu, gs, status = run_gpu(frames, v, occupancy=OCC, batch=batch)
+    assert status == 0
+    st = compare_occupancy(gpu, orc, len(frames), 0.85, name)
+    assert gs["voxel_updates"] == oc["total_updates"]
+    _record(name, st)
+    return st
+
+
+def test_occupancy_tiny_and_room():
+    w = synth.config_tiny()
+    _occ_parity("occ_tiny", w.frames, w.voxel_size)
+    r = synth.config_room(n_frames=300)
+    _occ_parity("occ_room12", r.frames[:12], r.voxel_size)
+
+
+def test_occupancy_batched_pipelined():
+    r = synth.config_room(n_frames=300)
+    st = _occ_parity("occ_room40_piped", r.frames[60:100], r.voxel_size, batch=40)
+    assert st["blocks"] > 2000
+
+
+def test_occupancy_lidar():
+    prims = synth.outdoor_scene(4)
+    Ts = synth.trajectory(4, prims, 2, xy=(4.0, 36.0))
+    lid = synth.lidar64()
+    frames = []
+    for i, T in enumerate(Ts):
+        TL = synth.configs.rig_poses(T)[4]
+        frames.append(Frame(lid, TL, synth.render_frame(prims, lid, TL, {"sigma": 0.02}, 4, i)))
+    _occ_parity("occ_lidar", frames, 0.05)
