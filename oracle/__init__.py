@@ -49,6 +49,7 @@ def _load():
             lib.orc_destroy.argtypes = [P]
             lib.orc_set_lidar_sampling.argtypes = [P, I, F]
             lib.orc_set_occupancy.argtypes = [P, F, F]
+            lib.orc_set_weighting.argtypes = [P, I, F]
             lib.orc_integrate_pinhole.argtypes = [P, P, I, I, F, F, F, F, P]
             lib.orc_integrate_pinhole.restype = I
             lib.orc_integrate_lidar.argtypes = [P, P, I, I, F, F, F, F, F, P]
@@ -96,6 +97,11 @@ class OracleMap:
 
     def set_lidar_sampling(self, nearest: bool = False, guard: float = 0.0):
         self._lib.orc_set_lidar_sampling(self._h, int(nearest), guard)
+
+    def set_weighting(self, mode: int, dropoff: float = 0.0):
+        """TSDF weight f_w: 0 constant, 1 inverse square depth, 2 constant with
+        drop-off behind the surface, 3 both."""
+        self._lib.orc_set_weighting(self._h, mode, dropoff)
 
     def set_occupancy(self, l_occ: float, l_free: float):
         """Occupancy layer: D becomes the log-odds, W the number of updates."""

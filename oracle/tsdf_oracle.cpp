@@ -15,8 +15,9 @@
  *     projected into the image (Eq. 1; pinhole Eq. 2, LiDAR Eq. 3), the depth
  *     is sampled (nearest pixel for a camera, guarded bilinear for LiDAR),
  *     d_p = d - d_v is formed, voxels with d_p < -tau are skipped, d_p is
- *     clamped to +tau, and the weighted running average with constant weight
- *     1 is applied, weights added up to max_weight (Sec. IV-B);
+ *     clamped to +tau, and the weighted running average is applied with the
+ *     weight f_w (constant 1 by default; optional sensor-error models),
+ *     weights added up to max_weight (Sec. IV-B);
  *   - occupancy layer (Sec. IV-B, second functor), optional: the same voxels
  *     instead add a constant log-odds, negative in front of the surface
  *     (d_p > 0), positive otherwise.
@@ -108,6 +109,9 @@ struct Oracle {
   // the number of updates
   int occupancy = 0;
   double l_occ = 0.0, l_free = 0.0;
+  // weighting function of the TSDF update
+  int weighting = 0;
+  double dropoff = 0.0;
   std::unordered_map<Key, std::unique_ptr<Block>, KeyHash> blocks;
   Counters last;
   int64_t total_updates = 0;
@@ -251,10 +255,21 @@ void insert_band(Oracle& m, const Pose& P, const std::vector<std::vector<Key>>& 
 
 /* Running weighted average with constant weight 1, weights added up to the
  * maximum; the average uses the unclamped sum W + 1 (Sec. IV-B). */
-inline void tsdf_update(double& D, double& W, double s, double wmax) {
-  const double w = 1.0;
+inline void tsdf_update(double& D, double& W, double s, double w, double wmax) {
+  if (!(W + w > 0.0)) return;  // zero weight on an unobserved voxel
   D = (W * D + w * s) / (W + w);
   W = std::min(W + w, wmax);
+}
+
+/* Weighting function f_w (Sec. IV-B: constant or from the sensor's error
+ * model): mode 0 constant 1; 1 inverse square of the voxel depth d_v; 2
+ * constant with a linear drop-off behind the surface, from 1 at
+ * d_p = -delta to 0 at d_p = -tau; 3 inverse square times that drop-off.
+ * dp is the projective distance before truncation. */
+inline double weight(int mode, double dv, double dp, double delta, double tau) {
+  double w = (mode == 1 || mode == 3) ? 1.0 / (dv * dv) : 1.0;
+  if ((mode == 2 || mode == 3) && dp < -delta) w *= (tau + dp) / (tau - delta);
+  return w;
 }
 
 /* Occupancy functor (Sec. IV-B): running addition of a constant negative
@@ -284,6 +299,14 @@ void* orc_create(float voxel_size, int32_t truncation_voxels, float max_weight) 
 }
 
 void orc_destroy(void* h) { delete static_cast<Oracle*>(h); }
+
+/* Weighting function of the TSDF update (see weight()); dropoff is the
+ * distance behind the surface where the drop-off starts (<= 0: one voxel). */
+void orc_set_weighting(void* h, int32_t mode, float dropoff) {
+  auto* m = static_cast<Oracle*>(h);
+  m->weighting = mode;
+  m->dropoff = dropoff > 0.0f ? (double)dropoff : m->vd;
+}
 
 /* Occupancy layer: voxels accumulate log-odds l_occ (on or behind the
  * surface, within tau) or l_free (in front of it) instead of the TSDF; the
@@ -387,8 +410,9 @@ int32_t orc_integrate_pinhole(void* h, const float* depth, int32_t W, int32_t H,
           if (m.occupancy) {
             occupancy_update(blk->D[l], blk->W[l], d - p[2] > 0.0f, m.l_occ, m.l_free);
           } else {
-            const double s = std::min((double)d - pC[2], m.taud);
-            tsdf_update(blk->D[l], blk->W[l], s, (double)m.wmax);
+            const double dp = (double)d - pC[2];
+            tsdf_update(blk->D[l], blk->W[l], std::min(dp, m.taud),
+                        weight(m.weighting, pC[2], dp, m.dropoff, m.taud), (double)m.wmax);
           }
           ++updated;
         }
@@ -530,8 +554,9 @@ int32_t orc_integrate_lidar(void* h, const float* range, int32_t n_az, int32_t n
           if (m.occupancy) {
             occupancy_update(blk->D[l], blk->W[l], dsamp32 - r > 0.0f, m.l_occ, m.l_free);
           } else {
-            const double s = std::min(dsamp64 - r64, m.taud);
-            tsdf_update(blk->D[l], blk->W[l], s, (double)m.wmax);
+            const double dp = dsamp64 - r64;
+            tsdf_update(blk->D[l], blk->W[l], std::min(dp, m.taud),
+                        weight(m.weighting, r64, dp, m.dropoff, m.taud), (double)m.wmax);
           }
           ++updated;
         }

@@ -477,3 +477,57 @@ def test_occupancy_lidar_sphere():
     np.testing.assert_array_equal(N[ok], seen[ok].astype(float))
     np.testing.assert_allclose(L[ok], np.where(seen, np.where(dp > 0, L_FREE, L_OCC), 0)[ok],
                                rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------- weighting functions
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_weighted_average_closed_form(mode):
+    """Sensor-error weights (Sec. IV-B, w = f_w(d_p)): two frames, the second
+    taken 0.3 m further back and with the plane moved 6 cm, so the voxel
+    depth d_v, the truncated distance s and the weight all differ between
+    the frames; D must be the weighted mean (w_A s_A + w_B s_B) / (w_A + w_B)
+    and W the weight sum, with w = 1 / d_v^2 (inverse square) and / or a
+    linear drop-off from 1 at d_p = -delta to 0 at d_p = -tau."""
+    cam = synth.pinhole(48, 36, 40.0)
+    TA = np.eye(4)
+    TB = np.eye(4)
+    TB[2, 3] = -0.3
+    imgA = synth.render_pinhole(scene(prim(PLANE, 0, 0, 1, 2.0)), TA, cam["fu"], cam["fv"],
+                                cam["cu"], cam["cv"], 48, 36)
+    imgB = synth.render_pinhole(scene(prim(PLANE, 0, 0, 1, 2.06)), TB, cam["fu"], cam["fv"],
+                                cam["cu"], cam["cv"], 48, 36)
+    v = F32(0.05)
+    tau = _tau(v)
+    delta = v
+    m = oracle.OracleMap(0.05)
+    m.set_weighting(mode)
+    m.integrate(cam, TA, imgA)
+    m.integrate(cam, TB, imgB)
+    keys, D, W = m.export()
+    pL = G.voxel_centres(keys, v)
+    num = np.zeros(D.shape)
+    den = np.zeros(D.shape)
+    ok = np.ones(D.shape, bool)
+    for T, img in ((TA, imgA), (TB, imgB)):
+        pC = G.to_sensor(T, pL)
+        i, j, inside, okp = G.pinhole_pixel(cam, pC, 1e-3)
+        d = img[np.clip(j, 0, 35), np.clip(i, 0, 47)].astype(np.float64)
+        dp = d - pC[..., 2]
+        ok &= okp & (np.abs(dp + tau) > 1e-5) & (np.abs(dp + delta) > 1e-6)
+        upd = inside & (dp >= -tau)
+        w = np.ones(D.shape)
+        if mode in (1, 3):
+            w = w / pC[..., 2] ** 2
+        if mode in (2, 3):
+            w = np.where(dp < -delta, w * (tau + dp) / (tau - delta), w)
+        num += np.where(upd, w * np.minimum(dp, tau), 0.0)
+        den += np.where(upd, w, 0.0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        D_exp = np.where(den > 0, num / den, 0.0)
+    assert ok.mean() > 0.9
+    np.testing.assert_allclose(W[ok], den[ok], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(D[ok], D_exp[ok], rtol=0, atol=1e-12)
+    # the weights really vary: fractional weight sums occur
+    assert np.any(np.abs(den[ok] - np.round(den[ok])) > 1e-3)
