@@ -82,6 +82,12 @@ enum { TSDF_STORAGE_FP32 = 0, TSDF_STORAGE_FP16 = 1 };
  * otherwise; `storage` is ignored, exported distances are the log-odds and
  * exported / queried weights are 0. */
 enum { TSDF_LAYER_TSDF = 0, TSDF_LAYER_OCCUPANCY = 1 };
+/* TSDF weighting functions (Sec. IV-B: w = f_w(d_p), constant or from the
+ * sensor's error model), combinable: the weight is 1, times 1 / d_v^2 with
+ * TSDF_WEIGHT_INV_SQUARE, times a linear drop-off from 1 at d_p = -dropoff to
+ * 0 at d_p = -tau with TSDF_WEIGHT_DROPOFF.  Non-constant weights are not
+ * integers: with FP16 storage W is then rounded to 11 significant bits. */
+enum { TSDF_WEIGHT_CONSTANT = 0, TSDF_WEIGHT_INV_SQUARE = 1, TSDF_WEIGHT_DROPOFF = 2 };
 enum { TSDF_SENSOR_PINHOLE = 0, TSDF_SENSOR_LIDAR = 1 };
 
 /* Map options.  max_blocks: pool size in blocks (4 KiB per block in FP32,
@@ -106,6 +112,8 @@ typedef struct {
   int32_t integrate_ctas_per_sm;
   int32_t layer;       /* TSDF_LAYER_TSDF or TSDF_LAYER_OCCUPANCY */
   float l_occ, l_free; /* occupancy: log-odds added per update (0, 0: 0.85, -0.4) */
+  int32_t weighting;   /* TSDF weight f_w, TSDF_WEIGHT_* flags (0 = constant 1) */
+  float dropoff;       /* drop-off start behind the surface, m (<= 0: one voxel) */
 } tsdf_map_opts;
 
 /* One frame of a batch.  `map` indexes the maps array of integrate_batch;

@@ -27,6 +27,7 @@ __all__ = ["TsdfError", "Pinhole", "Lidar", "MapOpts", "FrameDesc", "TsdfMap", "
 
 STORAGE_FP32, STORAGE_FP16 = 0, 1
 LAYER_TSDF, LAYER_OCCUPANCY = 0, 1
+WEIGHT_CONSTANT, WEIGHT_INV_SQUARE, WEIGHT_DROPOFF = 0, 1, 2
 STATIC_MAX_BLOCKS = 1 << 16  # TSDF_STATIC_MAX_BLOCKS
 SENSOR_PINHOLE, SENSOR_LIDAR = 0, 1
 _STATUS = {0: "TSDF_OK", -1: "TSDF_ERR_ARG", -2: "TSDF_ERR_CUDA", -3: "TSDF_ERR_CAPACITY",
@@ -60,7 +61,8 @@ class MapOpts(ctypes.Structure):
                 ("hash_capacity", ctypes.c_int64), ("lidar_nearest", ctypes.c_int32),
                 ("lidar_guard", ctypes.c_float), ("alloc_tile_h", ctypes.c_int32),
                 ("integrate_ctas_per_sm", ctypes.c_int32), ("layer", ctypes.c_int32),
-                ("l_occ", ctypes.c_float), ("l_free", ctypes.c_float)]
+                ("l_occ", ctypes.c_float), ("l_free", ctypes.c_float),
+                ("weighting", ctypes.c_int32), ("dropoff", ctypes.c_float)]
 
 
 class FrameDesc(ctypes.Structure):
@@ -165,10 +167,11 @@ def map_create(voxel_size: float, truncation_voxels: int, max_weight: float) -> 
 
 def map_create_ex(voxel_size, truncation_voxels, max_weight, storage=STORAGE_FP32, max_blocks=0,
                   hash_capacity=0, lidar_nearest=False, lidar_guard=0.0, alloc_tile_h=0,
-                  integrate_ctas_per_sm=0, layer=LAYER_TSDF, l_occ=0.0, l_free=0.0) -> int:
+                  integrate_ctas_per_sm=0, layer=LAYER_TSDF, l_occ=0.0, l_free=0.0,
+                  weighting=WEIGHT_CONSTANT, dropoff=0.0) -> int:
     h = ctypes.c_void_p()
     o = MapOpts(storage, max_blocks, hash_capacity, int(lidar_nearest), lidar_guard, alloc_tile_h,
-                integrate_ctas_per_sm, layer, l_occ, l_free)
+                integrate_ctas_per_sm, layer, l_occ, l_free, weighting, dropoff)
     _check(lib().map_create_ex(voxel_size, truncation_voxels, max_weight, ctypes.byref(o),
                                ctypes.byref(h)), "map_create_ex")
     return h.value
@@ -265,10 +268,11 @@ class TsdfMap:
                  storage: int = STORAGE_FP32, max_blocks: int = 0, hash_capacity: int = 0,
                  lidar_nearest: bool = False, lidar_guard: float = 0.0, alloc_tile_h: int = 0,
                  integrate_ctas_per_sm: int = 0, layer: int = LAYER_TSDF, l_occ: float = 0.0,
-                 l_free: float = 0.0):
+                 l_free: float = 0.0, weighting: int = WEIGHT_CONSTANT, dropoff: float = 0.0):
         self.handle = map_create_ex(voxel_size, truncation_voxels, max_weight, storage,
                                     max_blocks, hash_capacity, lidar_nearest, lidar_guard,
-                                    alloc_tile_h, integrate_ctas_per_sm, layer, l_occ, l_free)
+                                    alloc_tile_h, integrate_ctas_per_sm, layer, l_occ, l_free,
+                                    weighting, dropoff)
         self.voxel_size = voxel_size
         self.storage = storage
 

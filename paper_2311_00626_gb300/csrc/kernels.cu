@@ -410,12 +410,24 @@ __device__ __forceinline__ bool sample(const FrameDev& F, const MapDev& m, float
   return true;
 }
 
-// TSDF update functor (Sec. IV-B): weighted running average with weight 1,
-// the average taken with the unclamped weight sum, then weights capped.
-__device__ __forceinline__ void fuse(float& D, float& W, float s, float wmax) {
-  const float wn = W + 1.0f;
-  D = D + __fdividef(s - D, wn);
+// TSDF update functor (Sec. IV-B): weighted running average, the average
+// taken with the unclamped weight sum, then weights capped; a zero weight on
+// an unobserved voxel changes nothing.
+__device__ __forceinline__ void fuse(float& D, float& W, float s, float w, float wmax) {
+  const float wn = W + w;
+  if (!(wn > 0.0f)) return;
+  D = D + __fdividef(w * (s - D), wn);
   W = fminf(wn, wmax);
+}
+
+// Weight f_w(d_p) (Sec. IV-B: constant or from the sensor's error model):
+// 1, times 1 / d_v^2 for inverse-square weighting, times a linear drop-off
+// from 1 at d_p = -dropoff to 0 at d_p = -tau behind the surface.
+__device__ __forceinline__ float weight(const MapDev& m, float dv, float dp) {
+  float w = 1.0f;
+  if (m.weighting & 1) w = __fdividef(1.0f, dv * dv);
+  if ((m.weighting & 2) && dp < -m.dropoff) w *= __fdividef(m.tau + dp, m.tau - m.dropoff);
+  return w;
 }
 
 // Update functor of a voxel that passed the projection test, d_p >= -tau:
@@ -423,11 +435,11 @@ __device__ __forceinline__ void fuse(float& D, float& W, float s, float wmax) {
 // the running addition of l_free in front of the surface (d_p > 0) and
 // l_occ otherwise.
 template <int STORAGE>
-__device__ __forceinline__ void apply(const MapDev& m, float& D, float& W, float dp) {
+__device__ __forceinline__ void apply(const MapDev& m, float& D, float& W, float dv, float dp) {
   if (STORAGE == kStorageOcc)
     D += dp > 0.0f ? m.l_free : m.l_occ;
   else
-    fuse(D, W, fminf(dp, m.tau), m.wmax);
+    fuse(D, W, fminf(dp, m.tau), m.weighting ? weight(m, dv, dp) : 1.0f, m.wmax);
 }
 
 template <int STORAGE>
@@ -543,7 +555,7 @@ __device__ __forceinline__ void fuse_pinhole(const P& p, const int (&fq)[4], con
     for (int i = 0; i < 4; ++i) {
       const float dp = __fsub_rn(d[q][i], z[q][i]);
       if (d[q][i] > 0.0f && d[q][i] <= FLT_MAX && !(dp < -m.tau)) {
-        apply<STORAGE>(m, D[i], W[i], dp);
+        apply<STORAGE>(m, D[i], W[i], z[q][i], dp);
         ++upd;
       }
     }
@@ -561,7 +573,7 @@ __device__ __forceinline__ void fuse_any(const FrameDev& F, const MapDev& m, con
     if (!sample(F, m, px[i], py[i], pz[i], d, dv)) continue;
     const float dp = __fsub_rn(d, dv);
     if (dp < -m.tau) continue;
-    apply<STORAGE>(m, D[i], W[i], dp);
+    apply<STORAGE>(m, D[i], W[i], dv, dp);
     ++upd;
   }
 }

@@ -290,8 +290,13 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   if (!out || !(voxel_size > 0.0f) || !std::isfinite(voxel_size) || truncation_voxels <= 0 ||
       !(max_weight > 0.0f) || !std::isfinite(max_weight))
     return TSDF_ERR_ARG;
-  tsdf_map_opts o{TSDF_STORAGE_FP32, kDefaultBlocks, 0, 0, 0.0f, 0, 0, TSDF_LAYER_TSDF, 0.0f, 0.0f};
+  tsdf_map_opts o{TSDF_STORAGE_FP32, kDefaultBlocks, 0, 0, 0.0f, 0, 0, TSDF_LAYER_TSDF, 0.0f, 0.0f,
+                  TSDF_WEIGHT_CONSTANT, 0.0f};
   if (opts) o = *opts;
+  if (o.weighting < 0 || o.weighting > 3 || !std::isfinite(o.dropoff)) return TSDF_ERR_ARG;
+  if ((o.weighting & TSDF_WEIGHT_DROPOFF) &&
+      !((o.dropoff > 0.0f ? o.dropoff : voxel_size) < (float)((double)truncation_voxels * voxel_size)))
+    return TSDF_ERR_ARG;  // the drop-off must start in front of -tau
   if (o.layer != TSDF_LAYER_TSDF && o.layer != TSDF_LAYER_OCCUPANCY) return TSDF_ERR_ARG;
   if (!std::isfinite(o.l_occ) || !std::isfinite(o.l_free)) return TSDF_ERR_ARG;
   if (o.layer == TSDF_LAYER_OCCUPANCY) {
@@ -345,6 +350,8 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   d.guard = o.lidar_guard > 0.0f ? o.lidar_guard : d.tau;
   d.l_occ = o.l_occ;
   d.l_free = o.l_free;
+  d.weighting = o.weighting;
+  d.dropoff = o.dropoff > 0.0f ? o.dropoff : voxel_size;
   const size_t voxel_bytes = o.storage == TSDF_STORAGE_FP32 ? 8 : 4;
   bool ok = cudaMalloc(&d.keys, sizeof(unsigned long long) * cap) == cudaSuccess &&
             cudaMalloc(&d.vals, sizeof(int32_t) * cap) == cudaSuccess &&

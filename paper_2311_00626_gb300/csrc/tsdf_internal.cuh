@@ -72,6 +72,8 @@ struct MapDev {
   float wmax;
   float guard;                    // LiDAR bilinear guard (m)
   float l_occ, l_free;            // occupancy layer: log-odds added per update
+  int32_t weighting;              // TSDF weight: bit 0 inverse square depth, bit 1 drop-off
+  float dropoff;                  // drop-off start behind the surface (m)
 };
 
 // One frame as the kernels see it.  Geometry is anchor-relative: a is the

@@ -5,13 +5,15 @@ import numpy as np
 
 
 def run_oracle(frames, voxel_size, trunc=4, wmax=100.0, lidar_nearest=False, guard=0.0,
-               occupancy=None):
+               occupancy=None, weighting=0):
     import oracle
     m = oracle.OracleMap(voxel_size, trunc, wmax)
     if lidar_nearest or guard:
         m.set_lidar_sampling(lidar_nearest, guard)
     if occupancy is not None:
         m.set_occupancy(*occupancy)
+    if weighting:
+        m.set_weighting(weighting)
     cells = 0
     for f in frames:
         m.integrate(f.sensor, f.T, f.depth)
@@ -29,7 +31,7 @@ def to_device(frames):
 
 
 def run_gpu(frames, voxel_size, trunc=4, wmax=100.0, storage=0, batch=1, lidar_nearest=False,
-            guard=0.0, max_blocks=0, keep=False, occupancy=None):
+            guard=0.0, max_blocks=0, keep=False, occupancy=None, weighting=0):
     """Integrate `frames` (in order) into a fresh map, `batch` frames per
     integrate_batch call (batch=1: integrate_depth / integrate_lidar)."""
     import torch
@@ -37,7 +39,7 @@ def run_gpu(frames, voxel_size, trunc=4, wmax=100.0, storage=0, batch=1, lidar_n
     occ = {} if occupancy is None else {"layer": gt.LAYER_OCCUPANCY, "l_occ": occupancy[0],
                                         "l_free": occupancy[1]}
     m = gt.TsdfMap(voxel_size, trunc, wmax, storage=storage, max_blocks=max_blocks,
-                   lidar_nearest=lidar_nearest, lidar_guard=guard, **occ)
+                   lidar_nearest=lidar_nearest, lidar_guard=guard, weighting=weighting, **occ)
     dev = to_device(frames)
     if batch == 1:
         for f, d in zip(frames, dev):
@@ -57,15 +59,19 @@ def run_gpu(frames, voxel_size, trunc=4, wmax=100.0, storage=0, batch=1, lidar_n
     return out, stats, status
 
 
-def compare(gpu, orc, tol_d, label=""):
-    """Block set and weights bit-exact; distances within tol_d (metres)
-    wherever the oracle's weight is nonzero; untouched voxels hold zeros."""
+def compare(gpu, orc, tol_d, label="", w_rtol=0.0):
+    """Block set and weights bit-exact (weights within w_rtol relative when
+    they are not integers); distances within tol_d (metres) wherever the
+    oracle's weight is nonzero; untouched voxels hold zeros."""
     gk, gD, gW = gpu
     ok, oD, oW = orc
     assert gk.shape == ok.shape, f"{label}: {len(gk)} blocks on the GPU, {len(ok)} in the oracle"
     np.testing.assert_array_equal(gk, ok, err_msg=f"{label}: block sets differ")
-    bad = np.count_nonzero(gW.astype(np.float64) != oW)
-    assert bad == 0, f"{label}: {bad} voxel weights differ"
+    if w_rtol:
+        np.testing.assert_allclose(gW, oW, rtol=w_rtol, atol=0, err_msg=f"{label}: weights")
+    else:
+        bad = np.count_nonzero(gW.astype(np.float64) != oW)
+        assert bad == 0, f"{label}: {bad} voxel weights differ"
     obs = oW > 0
     err = np.abs(gD[obs].astype(np.float64) - oD[obs]) if obs.any() else np.zeros(1)
     assert err.max() <= tol_d, f"{label}: max |dD| {err.max():.3e} > {tol_d:.3e}"

@@ -39,7 +39,7 @@ def test_struct_layouts_match_header():
     # sizes from the C layout rules of the header's structs
     assert ctypes.sizeof(gt.Pinhole) == 24
     assert ctypes.sizeof(gt.Lidar) == 28
-    assert ctypes.sizeof(gt.MapOpts) == 56
+    assert ctypes.sizeof(gt.MapOpts) == 64
     assert ctypes.sizeof(gt.FrameDesc) == 4 + 4 + 24 + 28 + 4 + 8 + 128
 
 

@@ -373,3 +373,40 @@ def test_occupancy_lidar():
         TL = synth.configs.rig_poses(T)[4]
         frames.append(Frame(lid, TL, synth.render_frame(prims, lid, TL, {"sigma": 0.02}, 4, i)))
     _occ_parity("occ_lidar", frames, 0.05)
+
+
+# ------------------------------------------------------ weighting functions
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_weighting_functions(mode):
+    """Sensor-error weights f_w (inverse square depth, drop-off behind the
+    surface, both).  Block sets exact.  Inverse square alone: weight sums
+    within 1e-5 relative (FP32 sums of non-integer weights), distances within
+    1e-4 voxel.  With the drop-off the weight depends on d_p itself, whose
+    FP32 error (up to 4 ulp of the 5 m maximum depth, eps) moves each weight
+    by up to eps / (tau - delta); the bounds add n eps / (tau - delta) to the
+    weight sums and n eps / (tau - delta) * 2 tau / W to the distances (the
+    sensitivity of a weighted mean), compared where W >= 0.05."""
+    r = synth.config_room(n_frames=300)
+    frames = r.frames[:24]
+    n = len(frames)
+    orc, oc = run_oracle(frames, r.voxel_size, weighting=mode)
+    gpu, gs, status = run_gpu(frames, r.voxel_size, weighting=mode, batch=24)
+    assert status == 0
+    assert gs["voxel_updates"] == oc["total_updates"]
+    if mode == 1:
+        st = compare(gpu, orc, tol_pinhole(r.voxel_size), f"weighting{mode}", w_rtol=1e-5)
+    else:
+        (gk, gD, gW), (ok, oD, oW) = gpu, orc
+        np.testing.assert_array_equal(gk, ok)
+        v = float(np.float32(r.voxel_size))
+        tau, delta = 4 * v, v
+        eps = 4 * float(np.spacing(np.float32(5.0)))
+        dw = n * eps / (tau - delta)
+        werr = np.abs(gW.astype(np.float64) - oW)
+        assert np.all(werr <= 1e-5 * oW + dw), werr.max()
+        sel = oW >= 0.05
+        derr = np.abs(gD.astype(np.float64) - oD)[sel]
+        assert np.all(derr <= tol_pinhole(r.voxel_size) + dw * 2 * tau / oW[sel]), derr.max()
+        st = {"blocks": len(gk), "max_err": float(derr.max()), "max_w_err": float(werr.max())}
+    _record(f"weighting{mode}", st)
