@@ -52,6 +52,10 @@ def _load():
             lib.orc_set_weighting.argtypes = [P, I, F]
             lib.orc_integrate_pinhole.argtypes = [P, P, I, I, F, F, F, F, P]
             lib.orc_integrate_pinhole.restype = I
+            lib.orc_integrate_color.argtypes = [P, P, P, I, I, F, F, F, F, P]
+            lib.orc_integrate_color.restype = I
+            lib.orc_export_color.argtypes = [P, P, L]
+            lib.orc_export_color.restype = L
             lib.orc_integrate_lidar.argtypes = [P, P, I, I, F, F, F, F, F, P]
             lib.orc_integrate_lidar.restype = I
             lib.orc_num_blocks.argtypes = [P]
@@ -123,6 +127,27 @@ class OracleMap:
                                                sensor["max_range"], _p(T))
         if rc != 0:
             raise RuntimeError(f"oracle integrate failed ({rc})")
+
+    def integrate_color(self, sensor: dict, T: np.ndarray, depth: np.ndarray, rgba: np.ndarray):
+        """Colour layer: a registered depth image and uint32 RGBA image (r in
+        the low byte); voxels within tau of the surface average their pixel's
+        colour."""
+        depth = np.ascontiguousarray(depth, np.float32)
+        rgba = np.ascontiguousarray(rgba, np.uint32)
+        T = np.ascontiguousarray(T, np.float64).reshape(16)
+        assert depth.shape == rgba.shape == (sensor["height"], sensor["width"])
+        rc = self._lib.orc_integrate_color(self._h, _p(depth), _p(rgba), sensor["width"],
+                                           sensor["height"], sensor["fu"], sensor["fv"],
+                                           sensor["cu"], sensor["cv"], _p(T))
+        if rc != 0:
+            raise RuntimeError(f"oracle integrate_color failed ({rc})")
+
+    def export_color(self) -> np.ndarray:
+        """float64 [n, 512, 3] colours, blocks in export order."""
+        n = self.num_blocks()
+        rgb = np.zeros((n, 512, 3), np.float64)
+        assert self._lib.orc_export_color(self._h, _p(rgb), n) == n
+        return rgb
 
     def num_blocks(self) -> int:
         return int(self._lib.orc_num_blocks(self._h))

@@ -85,6 +85,7 @@ struct KeyHash {
 struct Block {
   double D[512];
   double W[512];
+  double C[512][3];  // colour layer: running average of r, g, b
 };
 
 struct Counters {
@@ -241,7 +242,11 @@ void insert_band(Oracle& m, const Pose& P, const std::vector<std::vector<Key>>& 
     auto it = m.blocks.find(k);
     if (it == m.blocks.end()) {
       auto b = std::make_unique<Block>();
-      for (int i = 0; i < 512; ++i) { b->D[i] = 0.0; b->W[i] = 0.0; }
+      for (int i = 0; i < 512; ++i) {
+        b->D[i] = 0.0;
+        b->W[i] = 0.0;
+        b->C[i][0] = b->C[i][1] = b->C[i][2] = 0.0;
+      }
       band.push_back(b.get());
       m.blocks.emplace(k, std::move(b));
       m.last.new_blocks++;
@@ -270,6 +275,14 @@ inline double weight(int mode, double dv, double dp, double delta, double tau) {
   double w = (mode == 1 || mode == 3) ? 1.0 / (dv * dv) : 1.0;
   if ((mode == 2 || mode == 3) && dp < -delta) w *= (tau + dp) / (tau - delta);
   return w;
+}
+
+/* Colour functor: running average of the pixel's r, g, b with weight 1,
+ * weights added up to the maximum (the TSDF rule applied per channel). */
+inline void color_update(double* C, double& W, uint32_t rgba, double wmax) {
+  const double c[3] = {(double)(rgba & 255u), (double)((rgba >> 8) & 255u), (double)((rgba >> 16) & 255u)};
+  for (int k = 0; k < 3; ++k) C[k] = (W * C[k] + c[k]) / (W + 1.0);
+  W = std::min(W + 1.0, wmax);
 }
 
 /* Occupancy functor (Sec. IV-B): running addition of a constant negative
@@ -330,9 +343,15 @@ void orc_set_lidar_sampling(void* h, int32_t nearest, float guard) {
  * Integrate one pinhole z-depth image (row-major float[H][W]; d <= 0 or
  * non-finite = invalid) taken at pose T_LC (row-major 4x4, sensor-to-layer).
  */
-int32_t orc_integrate_pinhole(void* h, const float* depth, int32_t W, int32_t H, float fu,
-                              float fv, float cu, float cv, const double* T) {
-  Oracle& m = *static_cast<Oracle*>(h);
+}  // extern "C"
+
+namespace {
+
+/* One pinhole frame; with rgba != nullptr the frame feeds the colour layer:
+ * voxels within the truncation band on either side of the surface
+ * (-tau <= d_p <= tau) average the colour of their pixel, weight 1. */
+int32_t integrate_pinhole(Oracle& m, const float* depth, const uint32_t* rgba, int32_t W, int32_t H,
+                          float fu, float fv, float cu, float cv, const double* T) {
   const Pose P = make_pose(T, m.Bd);
   // block coordinates are 21-bit: the sensor's block must lie within 2^19
   for (int c = 0; c < 3; ++c)
@@ -401,6 +420,13 @@ int32_t orc_integrate_pinhole(void* h, const float* depth, int32_t W, int32_t H,
           const float d = depth[(size_t)(int)v * W + (int)u];
           if (!(d > 0.0f && d <= 3.402823466e38f)) continue;
           if (d - p[2] < -tau) continue;
+          if (rgba) {
+            if (d - p[2] > tau) continue;  // colour only near the surface
+            const uint32_t c = rgba[(size_t)(int)v * W + (int)u];
+            color_update(blk->C[l], blk->W[l], c, (double)m.wmax);
+            ++updated;
+            continue;
+          }
           // value arithmetic (FP64): d_v is the voxel's z-depth in the camera
           const int64_t g[3] = {b.x * 8 + lx, b.y * 8 + ly, b.z * 8 + lz};
           const double pL[3] = {((double)g[0] + 0.5) * m.vd, ((double)g[1] + 0.5) * m.vd,
@@ -420,6 +446,28 @@ int32_t orc_integrate_pinhole(void* h, const float* depth, int32_t W, int32_t H,
   m.last.voxels_updated = updated;
   m.total_updates += updated;
   return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+/*
+ * Integrate one pinhole z-depth image (row-major float[H][W]; d <= 0 or
+ * non-finite = invalid) taken at pose T_LC (row-major 4x4, sensor-to-layer).
+ */
+int32_t orc_integrate_pinhole(void* h, const float* depth, int32_t W, int32_t H, float fu,
+                              float fv, float cu, float cv, const double* T) {
+  return integrate_pinhole(*static_cast<Oracle*>(h), depth, nullptr, W, H, fu, fv, cu, cv, T);
+}
+
+/* Integrate a registered depth + colour pair (rgba: row-major uint32 [H][W],
+ * r in the low byte, then g, b; the top byte is ignored) into the colour
+ * layer: the exported D is unused, W counts the colour updates and
+ * orc_export_color returns the averaged colours. */
+int32_t orc_integrate_color(void* h, const float* depth, const uint32_t* rgba, int32_t W, int32_t H,
+                            float fu, float fv, float cu, float cv, const double* T) {
+  return integrate_pinhole(*static_cast<Oracle*>(h), depth, rgba, W, H, fu, fv, cu, cv, T);
 }
 
 /*
@@ -584,6 +632,18 @@ int64_t orc_export(void* h, int32_t* keys, double* D, double* W, int64_t cap) {
     if (D) std::memcpy(D + 512 * i, b->D, sizeof(b->D));
     if (W) std::memcpy(W + 512 * i, b->W, sizeof(b->W));
   }
+  return (int64_t)ks.size();
+}
+
+/* Colours of all blocks, sorted like orc_export: rgb [n][512][3]. */
+int64_t orc_export_color(void* h, double* rgb, int64_t cap) {
+  Oracle& m = *static_cast<Oracle*>(h);
+  std::vector<Key> ks;
+  for (auto& kv : m.blocks) ks.push_back(kv.first);
+  std::sort(ks.begin(), ks.end());
+  if ((int64_t)ks.size() > cap) return -1;
+  for (size_t i = 0; i < ks.size(); ++i)
+    std::memcpy(rgb + (size_t)1536 * i, m.blocks[ks[i]]->C, sizeof(double) * 1536);
   return (int64_t)ks.size();
 }
 

@@ -531,3 +531,43 @@ def test_weighted_average_closed_form(mode):
     np.testing.assert_allclose(D[ok], D_exp[ok], rtol=0, atol=1e-12)
     # the weights really vary: fractional weight sums occur
     assert np.any(np.abs(den[ok] - np.round(den[ok])) > 1e-3)
+
+
+# ----------------------------------------------------------- colour layer
+
+
+def _rgba(r, g, b):
+    return (np.asarray(r, np.uint32) | (np.asarray(g, np.uint32) << 8)
+            | (np.asarray(b, np.uint32) << 16) | np.uint32(255 << 24))
+
+
+def test_color_closed_form():
+    """Colour layer: voxels within tau of the surface (-tau <= d_p <= tau)
+    take the colour of the pixel they project to, averaged over frames with
+    weight 1; voxels further in front or behind are not coloured.  Two frames
+    of the plane z = 2 m with colour images r = column, g = row, b = 40 and
+    r = 200 - column, g = 2 row, b = 90: the colour is the per-channel mean."""
+    cam = synth.pinhole(64, 48, 50.0, 32.0, 24.0)
+    T = np.eye(4)
+    depth = synth.render_pinhole(scene(prim(PLANE, 0, 0, 1, 2.0)), T, cam["fu"], cam["fv"],
+                                 cam["cu"], cam["cv"], 64, 48)
+    jj, ii = np.mgrid[0:48, 0:64]
+    imgs = [_rgba(ii, jj, np.full_like(ii, 40)), _rgba(200 - ii, 2 * jj, np.full_like(ii, 90))]
+    m = oracle.OracleMap(0.05)
+    for img in imgs:
+        m.integrate_color(cam, T, depth, img)
+    keys, _, W = m.export()
+    C = m.export_color()
+    v = F32(0.05)
+    tau = _tau(v)
+    pC = G.to_sensor(T, G.voxel_centres(keys, v))
+    i, j, inside, ok = G.pinhole_pixel(cam, pC, 1e-3)
+    dp = float(np.float32(2.0)) - pC[..., 2]
+    ok &= (np.abs(np.abs(dp) - tau) > 1e-5)
+    col = inside & (np.abs(dp) <= tau)
+    ic, jc = np.clip(i, 0, 63), np.clip(j, 0, 47)
+    exp = np.stack([(ic + (200 - ic)) / 2.0, (jc + 2 * jc) / 2.0, np.full(ic.shape, 65.0)], -1)
+    np.testing.assert_array_equal(W[ok], np.where(col, 2.0, 0.0)[ok])
+    np.testing.assert_allclose(C[ok & col], exp[ok & col], rtol=0, atol=1e-12)
+    assert np.all(C[ok & ~col] == 0)
+    assert (ok & col).sum() > 1000 and (ok & ~col & inside).sum() > 1000
