@@ -81,7 +81,15 @@ enum { TSDF_STORAGE_FP32 = 0, TSDF_STORAGE_FP16 = 1 };
  * adds l_free if it lies in front of the surface (d_p > 0) and l_occ
  * otherwise; `storage` is ignored, exported distances are the log-odds and
  * exported / queried weights are 0. */
-enum { TSDF_LAYER_TSDF = 0, TSDF_LAYER_OCCUPANCY = 1 };
+/* A colour layer (Sec. III: colour images C: Omega -> R^3; Table I: colour
+ * fusion) holds r, g, b and a colour weight per voxel (four FP32, 16 B):
+ * integrate_color fuses a colour image registered to a depth image (same
+ * intrinsics and pose); the depth image allocates the band like the TSDF,
+ * and every voxel within tau of the surface on both sides
+ * (-tau <= d_p <= tau) folds the colour of the pixel it projects to into a
+ * running average with weight 1, weights summed up to max_weight.  Colour
+ * maps take pinhole frames only; `storage` is ignored. */
+enum { TSDF_LAYER_TSDF = 0, TSDF_LAYER_OCCUPANCY = 1, TSDF_LAYER_COLOR = 2 };
 /* TSDF weighting functions (Sec. IV-B: w = f_w(d_p), constant or from the
  * sensor's error model), combinable: the weight is 1, times 1 / d_v^2 with
  * TSDF_WEIGHT_INV_SQUARE, times a linear drop-off from 1 at d_p = -dropoff to
@@ -110,7 +118,7 @@ typedef struct {
   float lidar_guard;
   int32_t alloc_tile_h;
   int32_t integrate_ctas_per_sm;
-  int32_t layer;       /* TSDF_LAYER_TSDF or TSDF_LAYER_OCCUPANCY */
+  int32_t layer;       /* TSDF_LAYER_TSDF, _OCCUPANCY or _COLOR */
   float l_occ, l_free; /* occupancy: log-odds added per update (0, 0: 0.85, -0.4) */
   int32_t weighting;   /* TSDF weight f_w, TSDF_WEIGHT_* flags (0 = constant 1) */
   float dropoff;       /* drop-off start behind the surface, m (<= 0: one voxel) */
@@ -119,7 +127,9 @@ typedef struct {
 /* One frame of a batch.  `map` indexes the maps array of integrate_batch;
  * `kind` selects which intrinsics member is read; depth_dev is the image
  * (row-major [height][width] z-depth or [n_el][n_az] range, float32);
- * T_world_sensor is the sensor-to-layer pose T_LC. */
+ * T_world_sensor is the sensor-to-layer pose T_LC; color_dev is the
+ * registered colour image (uint32 [height][width], r in the low byte, then
+ * g, b; the top byte is ignored): required for colour maps, NULL otherwise. */
 typedef struct {
   int32_t map;
   int32_t kind;
@@ -127,6 +137,7 @@ typedef struct {
   tsdf_lidar lidar;
   const float* depth_dev;
   double T_world_sensor[16];
+  const uint32_t* color_dev;
 } tsdf_frame_desc;
 
 /*
@@ -169,6 +180,16 @@ tsdf_status integrate_lidar(tsdf_map* map, const float* range_dev, const tsdf_li
                             const double T_world_lidar[16], void* cuda_stream);
 
 /*
+ * integrate_color — integrate one registered depth + colour pair into a
+ * colour map (see TSDF_LAYER_COLOR): depth_dev as for integrate_depth,
+ * color_dev uint32 [height][width] (r in the low byte, then g, b).  Returns
+ * TSDF_ERR_ARG for a map of another layer.  Async on cuda_stream.
+ */
+tsdf_status integrate_color(tsdf_map* map, const float* depth_dev, const uint32_t* color_dev,
+                            const tsdf_pinhole* intr, const double T_world_cam[16],
+                            void* cuda_stream);
+
+/*
  * integrate_batch — integrate n frames (any mix of sensors, sizes and maps)
  * in sub-batches of up to 32 frames, each one allocation launch and one
  * integration launch; with more than 32 frames the allocation of a
@@ -186,10 +207,20 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
  * query_voxels — TSDF value at n points (float32 [n][3], layer frame,
  * metres): the voxel containing each point, looked up in the block hash.
  * Writes dist_dev[n] and weight_dev[n]; unallocated or unobserved voxels
- * give weight 0 and distance 0.  Async on cuda_stream.
+ * give weight 0 and distance 0.  TSDF_ERR_ARG for a colour map (use
+ * query_color).  Async on cuda_stream.
  */
 tsdf_status query_voxels(const tsdf_map* map, const float* pts_dev, int64_t n, float* dist_dev,
                          float* weight_dev, void* cuda_stream);
+
+/*
+ * query_color — colour at n points of a colour map: rgb_dev float32 [n][3]
+ * (r, g, b in 0..255) and weight_dev[n] (colour updates, capped); zeros for
+ * unallocated or uncoloured voxels.  TSDF_ERR_ARG for a map of another
+ * layer.  Async on cuda_stream.
+ */
+tsdf_status query_color(const tsdf_map* map, const float* pts_dev, int64_t n, float* rgb_dev,
+                        float* weight_dev, void* cuda_stream);
 
 /* map_sync — wait for all work the library enqueued for this map and return
  * its sticky device status (TSDF_OK, TSDF_ERR_CAPACITY or TSDF_ERR_TIMEOUT). */
@@ -222,10 +253,17 @@ tsdf_status map_kernel_times(tsdf_map* map, double out_ms[2], int64_t* calls);
  * map_export — copy every allocated block to host memory, sorted by block
  * coordinates (x, then y, then z): keys_host int32 [n][3], dist_host and
  * weight_host float32 [n][512] (either may be NULL).  n must equal the block
- * count; returns TSDF_ERR_ARG otherwise.  Synchronises.
+ * count; returns TSDF_ERR_ARG otherwise.  For a colour map the distances are
+ * 0 and the weights are the colour weights.  Synchronises.
  */
 tsdf_status map_export(const tsdf_map* map, int32_t* keys_host, float* dist_host,
                        float* weight_host, int64_t n);
+
+/* map_export_color — as map_export for a colour map: keys_host int32 [n][3],
+ * rgb_host float32 [n][512][3], weight_host float32 [n][512] (either may be
+ * NULL).  TSDF_ERR_ARG for a map of another layer or a wrong n. */
+tsdf_status map_export_color(const tsdf_map* map, int32_t* keys_host, float* rgb_host,
+                             float* weight_host, int64_t n);
 
 /* map_reset — drop every block (keeps the allocation), enqueued on
  * cuda_stream; clears the sticky status. */

@@ -22,11 +22,12 @@ __all__ = ["TsdfError", "Pinhole", "Lidar", "MapOpts", "FrameDesc", "TsdfMap", "
            "integrate_batch", "query_voxels", "map_sync", "map_num_blocks", "map_stats",
            "map_export", "map_reset", "map_destroy", "map_timing", "map_kernel_times",
            "MapBuffers", "integrate_depth_static", "STATIC_MAX_BLOCKS", "LAYER_TSDF",
-           "LAYER_OCCUPANCY", "STORAGE_FP32", "STORAGE_FP16",
+           "LAYER_OCCUPANCY", "LAYER_COLOR", "STORAGE_FP32", "STORAGE_FP16",
+           "integrate_color", "query_color", "map_export_color",
            "SENSOR_PINHOLE", "SENSOR_LIDAR", "EXPORTED_SYMBOLS"]
 
 STORAGE_FP32, STORAGE_FP16 = 0, 1
-LAYER_TSDF, LAYER_OCCUPANCY = 0, 1
+LAYER_TSDF, LAYER_OCCUPANCY, LAYER_COLOR = 0, 1, 2
 WEIGHT_CONSTANT, WEIGHT_INV_SQUARE, WEIGHT_DROPOFF = 0, 1, 2
 STATIC_MAX_BLOCKS = 1 << 16  # TSDF_STATIC_MAX_BLOCKS
 SENSOR_PINHOLE, SENSOR_LIDAR = 0, 1
@@ -35,7 +36,8 @@ _STATUS = {0: "TSDF_OK", -1: "TSDF_ERR_ARG", -2: "TSDF_ERR_CUDA", -3: "TSDF_ERR_
 EXPORTED_SYMBOLS = ["map_create", "map_create_ex", "integrate_depth", "integrate_lidar",
                     "integrate_batch", "query_voxels", "map_sync", "map_num_blocks", "map_stats",
                     "map_export", "map_reset", "map_destroy", "map_timing", "map_kernel_times",
-                    "integrate_depth_static"]
+                    "integrate_depth_static", "integrate_color", "query_color",
+                    "map_export_color"]
 
 
 class TsdfError(RuntimeError):
@@ -68,7 +70,7 @@ class MapOpts(ctypes.Structure):
 class FrameDesc(ctypes.Structure):
     _fields_ = [("map", ctypes.c_int32), ("kind", ctypes.c_int32), ("pinhole", Pinhole),
                 ("lidar", Lidar), ("depth_dev", ctypes.c_void_p),
-                ("T_world_sensor", ctypes.c_double * 16)]
+                ("T_world_sensor", ctypes.c_double * 16), ("color_dev", ctypes.c_void_p)]
 
 
 class MapBuffers(ctypes.Structure):
@@ -111,6 +113,9 @@ def lib():
                 "map_kernel_times": ([P, P, ctypes.POINTER(ctypes.c_int64)], I),
                 "integrate_depth_static": ([ctypes.POINTER(MapBuffers), F, I, F, P,
                                             ctypes.POINTER(Pinhole), P, P], I),
+                "integrate_color": ([P, P, P, ctypes.POINTER(Pinhole), P, P], I),
+                "query_color": ([P, P, L64, P, P, P], I),
+                "map_export_color": ([P, P, P, P, L64], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -187,6 +192,13 @@ def integrate_lidar(m: int, rng, intr: Lidar, T_world_lidar, stream=None):
                                  _stream(stream)), "integrate_lidar")
 
 
+def integrate_color(m: int, depth, rgba, intr: Pinhole, T_world_cam, stream=None):
+    """depth: float32 [H, W] device tensor; rgba: uint32 (int32) [H, W] device
+    tensor, r in the low byte."""
+    _check(lib().integrate_color(m, _dptr(depth), _dptr(rgba), ctypes.byref(intr),
+                                 _pose(T_world_cam), _stream(stream)), "integrate_color")
+
+
 def integrate_batch(maps, frames, stream=None):
     """maps: sequence of map handles; frames: sequence of FrameDesc."""
     arr_m = (ctypes.c_void_p * len(maps))(*maps)
@@ -199,6 +211,12 @@ def query_voxels(m: int, pts, dist, weight, stream=None):
     n = pts.shape[0] if hasattr(pts, "shape") else 0
     _check(lib().query_voxels(m, _dptr(pts), n, _dptr(dist), _dptr(weight), _stream(stream)),
            "query_voxels")
+
+
+def query_color(m: int, pts, rgb, weight, stream=None):
+    n = pts.shape[0] if hasattr(pts, "shape") else 0
+    _check(lib().query_color(m, _dptr(pts), n, _dptr(rgb), _dptr(weight), _stream(stream)),
+           "query_color")
 
 
 def map_sync(m: int) -> int:
@@ -243,6 +261,17 @@ def map_export(m: int, with_values: bool = True):
     return keys, D, W
 
 
+def map_export_color(m: int):
+    """(keys int32[n,3] sorted by (x,y,z), rgb float32[n,512,3], W float32[n,512])."""
+    n = map_num_blocks(m)
+    keys = np.zeros((n, 3), np.int32)
+    rgb = np.zeros((n, 512, 3), np.float32)
+    W = np.zeros((n, 512), np.float32)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(lib().map_export_color(m, vp(keys), vp(rgb), vp(W), n), "map_export_color")
+    return keys, rgb, W
+
+
 def map_reset(m: int, stream=None):
     _check(lib().map_reset(m, _stream(stream)), "map_reset")
 
@@ -282,8 +311,11 @@ class TsdfMap:
         else:
             integrate_lidar(self.handle, depth, lidar(sensor), T, stream)
 
-    def frame_desc(self, index: int, sensor: dict, T, depth) -> FrameDesc:
-        return frame_desc(index, sensor, T, depth)
+    def integrate_color(self, sensor: dict, T, depth, rgba, stream=None):
+        integrate_color(self.handle, depth, rgba, pinhole(sensor), T, stream)
+
+    def frame_desc(self, index: int, sensor: dict, T, depth, rgba=None) -> FrameDesc:
+        return frame_desc(index, sensor, T, depth, rgba)
 
     def sync(self) -> int:
         return map_sync(self.handle)
@@ -297,8 +329,14 @@ class TsdfMap:
     def export(self, with_values: bool = True):
         return map_export(self.handle, with_values)
 
+    def export_color(self):
+        return map_export_color(self.handle)
+
     def query(self, pts, dist, weight, stream=None):
         query_voxels(self.handle, pts, dist, weight, stream)
+
+    def query_color(self, pts, rgb, weight, stream=None):
+        query_color(self.handle, pts, rgb, weight, stream)
 
     def reset(self, stream=None):
         map_reset(self.handle, stream)
@@ -315,7 +353,7 @@ class TsdfMap:
             pass
 
 
-def frame_desc(map_index: int, sensor: dict, T, depth) -> FrameDesc:
+def frame_desc(map_index: int, sensor: dict, T, depth, rgba=None) -> FrameDesc:
     fd = FrameDesc()
     fd.map = map_index
     if sensor["kind"] == "pinhole":
@@ -326,4 +364,5 @@ def frame_desc(map_index: int, sensor: dict, T, depth) -> FrameDesc:
         fd.lidar = lidar(sensor)
     fd.depth_dev = _dptr(depth)
     fd.T_world_sensor = _pose(T)
+    fd.color_dev = _dptr(rgba) if rgba is not None else None
     return fd

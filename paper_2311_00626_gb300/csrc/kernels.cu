@@ -442,19 +442,34 @@ __device__ __forceinline__ void apply(const MapDev& m, float& D, float& W, float
     fuse(D, W, fminf(dp, m.tau), m.weighting ? weight(m, dv, dp) : 1.0f, m.wmax);
 }
 
+// Colour functor: the running average of the pixel's r, g, b with weight 1
+// per frame (the TSDF average applied per channel), weights capped.
+__device__ __forceinline__ void apply_color(const MapDev& m, float& R, float& G, float& B, float& W,
+                                            uint32_t c) {
+  const float wn = W + 1.0f;
+  const float iw = __frcp_rn(wn);
+  R = __fmaf_rn(__fsub_rn((float)(c & 255u), R), iw, R);
+  G = __fmaf_rn(__fsub_rn((float)((c >> 8) & 255u), G), iw, G);
+  B = __fmaf_rn(__fsub_rn((float)((c >> 16) & 255u), B), iw, B);
+  W = fminf(wn, m.wmax);
+}
+
+// A thread's four voxels in registers: D and W (TSDF distance and weight,
+// occupancy log-odds, or colour red and weight) and, for colour only, G and B.
 template <int STORAGE>
 struct Voxels4;
 
 template <>
 struct Voxels4<kStorageF32> {
-  __device__ __forceinline__ static void load(const MapDev& m, int pool, int t, float* D, float* W) {
+  __device__ __forceinline__ static void load(const MapDev& m, int pool, int t, float* D, float* W,
+                                              float* G, float* B) {
     const float4* src = reinterpret_cast<const float4*>(m.pool) + (size_t)pool * 256 + 2 * t;
     const float4 a = src[0], b = src[1];
     D[0] = a.x; W[0] = a.y; D[1] = a.z; W[1] = a.w;
     D[2] = b.x; W[2] = b.y; D[3] = b.z; W[3] = b.w;
   }
   __device__ __forceinline__ static void store(const MapDev& m, int pool, int t, const float* D,
-                                               const float* W) {
+                                               const float* W, const float* G, const float* B) {
     float4* dst = reinterpret_cast<float4*>(m.pool) + (size_t)pool * 256 + 2 * t;
     dst[0] = make_float4(D[0], W[0], D[1], W[1]);
     dst[1] = make_float4(D[2], W[2], D[3], W[3]);
@@ -463,20 +478,22 @@ struct Voxels4<kStorageF32> {
 
 template <>
 struct Voxels4<kStorageOcc> {
-  __device__ __forceinline__ static void load(const MapDev& m, int pool, int t, float* D, float* W) {
+  __device__ __forceinline__ static void load(const MapDev& m, int pool, int t, float* D, float* W,
+                                              float* G, float* B) {
     const float4 a = reinterpret_cast<const float4*>(m.pool)[(size_t)pool * 128 + t];
     D[0] = a.x; D[1] = a.y; D[2] = a.z; D[3] = a.w;
     W[0] = W[1] = W[2] = W[3] = 0.0f;
   }
   __device__ __forceinline__ static void store(const MapDev& m, int pool, int t, const float* D,
-                                               const float* W) {
+                                               const float* W, const float* G, const float* B) {
     reinterpret_cast<float4*>(m.pool)[(size_t)pool * 128 + t] = make_float4(D[0], D[1], D[2], D[3]);
   }
 };
 
 template <>
 struct Voxels4<kStorageF16> {
-  __device__ __forceinline__ static void load(const MapDev& m, int pool, int t, float* D, float* W) {
+  __device__ __forceinline__ static void load(const MapDev& m, int pool, int t, float* D, float* W,
+                                              float* G, float* B) {
     const uint4 raw = reinterpret_cast<const uint4*>(m.pool)[(size_t)pool * 128 + t];
     const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
@@ -487,7 +504,7 @@ struct Voxels4<kStorageF16> {
     }
   }
   __device__ __forceinline__ static void store(const MapDev& m, int pool, int t, const float* D,
-                                               const float* W) {
+                                               const float* W, const float* G, const float* B) {
     uint32_t w4[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -495,6 +512,25 @@ struct Voxels4<kStorageF16> {
       w4[i] = *reinterpret_cast<const uint32_t*>(&h);
     }
     reinterpret_cast<uint4*>(m.pool)[(size_t)pool * 128 + t] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+  }
+};
+
+template <>
+struct Voxels4<kStorageColor> {
+  __device__ __forceinline__ static void load(const MapDev& m, int pool, int t, float* D, float* W,
+                                              float* G, float* B) {
+    const float4* src = reinterpret_cast<const float4*>(m.pool) + (size_t)pool * 512 + 4 * t;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 a = src[i];
+      D[i] = a.x; G[i] = a.y; B[i] = a.z; W[i] = a.w;
+    }
+  }
+  __device__ __forceinline__ static void store(const MapDev& m, int pool, int t, const float* D,
+                                               const float* W, const float* G, const float* B) {
+    float4* dst = reinterpret_cast<float4*>(m.pool) + (size_t)pool * 512 + 4 * t;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dst[i] = make_float4(D[i], G[i], B[i], W[i]);
   }
 };
 
@@ -526,14 +562,17 @@ __device__ __forceinline__ void row_points(const FrameDev& F, float v, const Vox
 }
 
 // NQ consecutive pinhole frames of the batch: phase 1 projects every voxel
-// into every frame (Eq. 2, nearest pixel) and issues all depth loads, phase 2
-// applies the updates in frame order.  An out-of-image projection reads no
-// pixel and yields d = 0, which is invalid like a missing depth.
+// into every frame (Eq. 2, nearest pixel) and issues all depth loads (and
+// colour loads for a colour layer), phase 2 applies the updates in frame
+// order.  An out-of-image projection reads no pixel and yields d = 0, which
+// is invalid like a missing depth.  A colour layer updates only voxels within
+// tau of the surface on both sides.
 template <int NQ, int STORAGE, class P>
 __device__ __forceinline__ void fuse_pinhole(const P& p, const int (&fq)[4], const MapDev& m,
-                                             const VoxelRow& r, float* D, float* W,
-                                             unsigned long long& upd) {
+                                             const VoxelRow& r, float* D, float* W, float* G,
+                                             float* B, unsigned long long& upd) {
   float d[NQ][4], z[NQ][4];
+  uint32_t c[NQ][4];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     const FrameDev& F = p.fr[fq[q]];
@@ -546,7 +585,13 @@ __device__ __forceinline__ void fuse_pinhole(const P& p, const int (&fq)[4], con
       const float v = __fadd_rn(__fmaf_rn(__fmul_rn(py[i], iz), F.fv, F.cv), 0.5f);
       const bool in = z[q][i] > 0.0f && u >= 0.0f && u < (float)F.width && v >= 0.0f &&
                       v < (float)F.height;
-      d[q][i] = in ? __ldg(F.depth + (int)v * F.width + (int)u) : 0.0f;
+      if (STORAGE == kStorageColor) {
+        const int pix = in ? (int)v * F.width + (int)u : 0;
+        d[q][i] = in ? __ldg(F.depth + pix) : 0.0f;
+        c[q][i] = in ? __ldg(F.rgba + pix) : 0u;
+      } else {
+        d[q][i] = in ? __ldg(F.depth + (int)v * F.width + (int)u) : 0.0f;
+      }
     }
   }
 #pragma unroll
@@ -555,16 +600,23 @@ __device__ __forceinline__ void fuse_pinhole(const P& p, const int (&fq)[4], con
     for (int i = 0; i < 4; ++i) {
       const float dp = __fsub_rn(d[q][i], z[q][i]);
       if (d[q][i] > 0.0f && d[q][i] <= FLT_MAX && !(dp < -m.tau)) {
-        apply<STORAGE>(m, D[i], W[i], z[q][i], dp);
+        if (STORAGE == kStorageColor) {
+          if (dp > m.tau) continue;
+          apply_color(m, D[i], G[i], B[i], W[i], c[q][i]);
+        } else {
+          apply<STORAGE>(m, D[i], W[i], z[q][i], dp);
+        }
         ++upd;
       }
     }
 }
 
-// One frame of any sensor kind, voxel by voxel.
+// One frame of any sensor kind, voxel by voxel (colour layers take pinhole
+// frames only, through fuse_pinhole).
 template <int STORAGE>
 __device__ __forceinline__ void fuse_any(const FrameDev& F, const MapDev& m, const VoxelRow& r,
                                          float* D, float* W, unsigned long long& upd) {
+  if (STORAGE == kStorageColor) return;
   float px[4], py[4], pz[4];
   row_points(F, m.v, r, px, py, pz);
 #pragma unroll
@@ -620,12 +672,12 @@ __global__ void __launch_bounds__(kIntegrateThreads)
     const int pool = fresh ? -val - 2 : val;
     unsigned long long my_upd = 0;
     if (val != -1) {
-      float D[4], W[4];
+      float D[4], W[4], G[4], B[4];
       if (fresh) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) { D[i] = 0.0f; W[i] = 0.0f; }
+        for (int i = 0; i < 4; ++i) { D[i] = 0.0f; W[i] = 0.0f; G[i] = 0.0f; B[i] = 0.0f; }
       } else {
-        Voxels4<STORAGE>::load(m, pool, t, D, W);
+        Voxels4<STORAGE>::load(m, pool, t, D, W, G, B);
       }
       const int bx = key_coord(slot_key, 0), by = key_coord(slot_key, 1), bz = key_coord(slot_key, 2);
       const VoxelRow vr{bx, by, bz, lx0, ly, lz};
@@ -652,11 +704,11 @@ __global__ void __launch_bounds__(kIntegrateThreads)
             }
           }
         }
-        if (nq == 4) fuse_pinhole<4, STORAGE>(p, fq, m, vr, D, W, my_upd);
+        if (nq == 4) fuse_pinhole<4, STORAGE>(p, fq, m, vr, D, W, G, B, my_upd);
         else if (nq >= 1) {
           for (int q = 0; q < nq; ++q) {
             const int fq1[4] = {fq[q], -1, -1, -1};
-            fuse_pinhole<1, STORAGE>(p, fq1, m, vr, D, W, my_upd);
+            fuse_pinhole<1, STORAGE>(p, fq1, m, vr, D, W, G, B, my_upd);
           }
         }
         else {
@@ -665,7 +717,7 @@ __global__ void __launch_bounds__(kIntegrateThreads)
           fuse_any<STORAGE>(p.fr[f], m, vr, D, W, my_upd);
         }
       }
-      Voxels4<STORAGE>::store(m, pool, t, D, W);
+      Voxels4<STORAGE>::store(m, pool, t, D, W, G, B);
     }
     // per-map update count: warp sums into a shared per-map counter
     for (int o = 16; o > 0; o >>= 1) my_upd += __shfl_down_sync(0xffffffffu, my_upd, o);
@@ -728,6 +780,33 @@ __global__ void query_kernel(const MapDev m, const float* __restrict__ pts, int6
   weight[i] = outW;
 }
 
+// Colour of the voxel holding each point: r, g, b and the colour weight;
+// zeros where no block or no colour update exists.
+__global__ void query_color_kernel(const MapDev m, const float* __restrict__ pts, int64_t n,
+                                   float* __restrict__ rgb, float* __restrict__ weight) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 out = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+  const float gx = floorf(__fdiv_rn(x, m.v)), gy = floorf(__fdiv_rn(y, m.v)), gz = floorf(__fdiv_rn(z, m.v));
+  const float lim = 8.0f * 1048576.0f;
+  if (fabsf(gx) < lim && fabsf(gy) < lim && fabsf(gz) < lim) {
+    const int ix = (int)gx, iy = (int)gy, iz = (int)gz;
+    const int slot = hash_find(m, pack_key(ix >> 3, iy >> 3, iz >> 3));
+    if (slot >= 0) {
+      const int val = m.vals[slot];
+      if (val >= 0) {
+        const int l = (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7);
+        out = reinterpret_cast<const float4*>(m.pool)[(size_t)val * 512 + l];
+      }
+    }
+  }
+  rgb[3 * i] = out.x;
+  rgb[3 * i + 1] = out.y;
+  rgb[3 * i + 2] = out.z;
+  weight[i] = out.w;
+}
+
 __global__ void reset_kernel(const MapDev m, uint32_t cap) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
     m.keys[i] = kEmptyKey;
@@ -753,7 +832,9 @@ cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile
 template <int NF, int NM>
 cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStream_t s) {
   // all maps of a batch share one storage type (checked by the host API)
-  if (p.maps[0].storage == kStorageOcc)
+  if (p.maps[0].storage == kStorageColor)
+    integrate_kernel<NF, NM, kStorageColor><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+  else if (p.maps[0].storage == kStorageOcc)
     integrate_kernel<NF, NM, kStorageOcc><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
   else if (p.maps[0].storage == kStorageF16)
     integrate_kernel<NF, NM, kStorageF16><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
@@ -783,6 +864,15 @@ cudaError_t launch_query(const MapDev& m, const float* pts, int64_t n, float* di
   return cudaGetLastError();
 }
 
+cudaError_t launch_query_color(const MapDev& m, const float* pts, int64_t n, float* rgb, float* weight,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  query_color_kernel<<<blocks, threads, 0, s>>>(m, pts, n, rgb, weight);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reset(const MapDev& m, uint32_t cap, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -794,7 +884,10 @@ cudaError_t launch_reset(const MapDev& m, uint32_t cap, cudaStream_t s) {
 int integrate_ctas_per_sm(int storage) {
   int n = 0;
   cudaError_t e;
-  if (storage == kStorageOcc)
+  if (storage == kStorageColor)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageColor>, kIntegrateThreads, 0);
+  else if (storage == kStorageOcc)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageOcc>, kIntegrateThreads, 0);
   else if (storage == kStorageF16)

@@ -156,13 +156,19 @@ tsdf_status lidar_table(tsdf_map* m, const tsdf_lidar* c, const float** out) {
   return TSDF_OK;
 }
 
+// A colour map takes pinhole frames with a colour image; other maps take no
+// colour image.
 tsdf_status fill_frame(tsdf_map* m, int map_index, int kind, const tsdf_pinhole* ph,
-                       const tsdf_lidar* li, const float* depth, const double* T, FrameDev& F) {
+                       const tsdf_lidar* li, const float* depth, const uint32_t* rgba,
+                       const double* T, FrameDev& F) {
   std::memset(&F, 0, sizeof(F));
   if (!depth || !T || !rigid(T)) return TSDF_ERR_ARG;
+  const bool color = m->storage == gbt::kStorageColor;
+  if (color != (rgba != nullptr) || (color && kind != TSDF_SENSOR_PINHOLE)) return TSDF_ERR_ARG;
   F.kind = kind;
   F.map = map_index;
   F.depth = depth;
+  F.rgba = rgba;
   if (kind == TSDF_SENSOR_PINHOLE) {
     if (!valid_pinhole(ph)) return TSDF_ERR_ARG;
     F.width = ph->width;
@@ -188,6 +194,10 @@ tsdf_status fill_frame(tsdf_map* m, int map_index, int kind, const tsdf_pinhole*
   }
   if (!prepare_pose(m->Bd, T, F)) return TSDF_ERR_ARG;
   return TSDF_OK;
+}
+
+size_t voxel_size_bytes(int storage) {
+  return storage == gbt::kStorageColor ? 16 : storage == TSDF_STORAGE_FP32 ? 8 : 4;
 }
 
 int alloc_ctas(const FrameDev& F, int tile_h) {
@@ -221,7 +231,7 @@ MapDev view_set(const tsdf_map* m, int set) {
 }
 
 tsdf_status integrate_one(tsdf_map* m, int kind, const tsdf_pinhole* ph, const tsdf_lidar* li,
-                          const float* depth, const double* T, void* stream) {
+                          const float* depth, const uint32_t* rgba, const double* T, void* stream) {
   if (!m) return TSDF_ERR_ARG;
   if (!on_device(m)) return TSDF_ERR_STATE;
   if (status_from_bits(m->status_seen) != TSDF_OK) return status_from_bits(m->status_seen);
@@ -230,7 +240,7 @@ tsdf_status integrate_one(tsdf_map* m, int kind, const tsdf_pinhole* ph, const t
   p.n_frames = 1;
   p.n_maps = 1;
   p.maps[0] = m->dev;
-  tsdf_status st = fill_frame(m, 0, kind, ph, li, depth, T, p.fr[0]);
+  tsdf_status st = fill_frame(m, 0, kind, ph, li, depth, rgba, T, p.fr[0]);
   if (st != TSDF_OK) return st;
   p.fr[0].blk_begin = 0;
   p.fr[0].bit = 0;
@@ -297,7 +307,8 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   if ((o.weighting & TSDF_WEIGHT_DROPOFF) &&
       !((o.dropoff > 0.0f ? o.dropoff : voxel_size) < (float)((double)truncation_voxels * voxel_size)))
     return TSDF_ERR_ARG;  // the drop-off must start in front of -tau
-  if (o.layer != TSDF_LAYER_TSDF && o.layer != TSDF_LAYER_OCCUPANCY) return TSDF_ERR_ARG;
+  if (o.layer != TSDF_LAYER_TSDF && o.layer != TSDF_LAYER_OCCUPANCY && o.layer != TSDF_LAYER_COLOR)
+    return TSDF_ERR_ARG;
   if (!std::isfinite(o.l_occ) || !std::isfinite(o.l_free)) return TSDF_ERR_ARG;
   if (o.layer == TSDF_LAYER_OCCUPANCY) {
     o.storage = gbt::kStorageOcc;
@@ -306,12 +317,19 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
       o.l_free = -0.4f;
     }
   }
+  if (o.layer == TSDF_LAYER_COLOR) {
+    o.storage = gbt::kStorageColor;
+    o.weighting = TSDF_WEIGHT_CONSTANT;
+  }
   if (o.alloc_tile_h != 0 && o.alloc_tile_h != gbt::kTileHSmall && o.alloc_tile_h != gbt::kTileHBig)
     return TSDF_ERR_ARG;
   if (o.integrate_ctas_per_sm < 0) return TSDF_ERR_ARG;
   if (o.storage != TSDF_STORAGE_FP32 && o.storage != TSDF_STORAGE_FP16 &&
-      o.storage != gbt::kStorageOcc)
+      o.storage != gbt::kStorageOcc && o.storage != gbt::kStorageColor)
     return TSDF_ERR_ARG;
+  if ((o.storage == gbt::kStorageOcc) != (o.layer == TSDF_LAYER_OCCUPANCY) ||
+      (o.storage == gbt::kStorageColor) != (o.layer == TSDF_LAYER_COLOR))
+    return TSDF_ERR_ARG;  // internal storage kinds go with their layer
   if (o.max_blocks <= 0) o.max_blocks = kDefaultBlocks;
   if (o.max_blocks > (1ll << 27)) return TSDF_ERR_ARG;
   int64_t cap = 1;
@@ -352,7 +370,7 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   d.l_free = o.l_free;
   d.weighting = o.weighting;
   d.dropoff = o.dropoff > 0.0f ? o.dropoff : voxel_size;
-  const size_t voxel_bytes = o.storage == TSDF_STORAGE_FP32 ? 8 : 4;
+  const size_t voxel_bytes = voxel_size_bytes(o.storage);
   bool ok = cudaMalloc(&d.keys, sizeof(unsigned long long) * cap) == cudaSuccess &&
             cudaMalloc(&d.vals, sizeof(int32_t) * cap) == cudaSuccess &&
             cudaMalloc(&d.mask, sizeof(uint32_t) * cap) == cudaSuccess &&
@@ -395,12 +413,22 @@ tsdf_status map_create(float voxel_size, int32_t truncation_voxels, float max_we
 
 tsdf_status integrate_depth(tsdf_map* map, const float* depth_dev, const tsdf_pinhole* intr,
                             const double T_world_cam[16], void* cuda_stream) {
-  return integrate_one(map, TSDF_SENSOR_PINHOLE, intr, nullptr, depth_dev, T_world_cam, cuda_stream);
+  return integrate_one(map, TSDF_SENSOR_PINHOLE, intr, nullptr, depth_dev, nullptr, T_world_cam,
+                       cuda_stream);
+}
+
+tsdf_status integrate_color(tsdf_map* map, const float* depth_dev, const uint32_t* color_dev,
+                            const tsdf_pinhole* intr, const double T_world_cam[16],
+                            void* cuda_stream) {
+  if (!map || !color_dev || map->storage != gbt::kStorageColor) return TSDF_ERR_ARG;
+  return integrate_one(map, TSDF_SENSOR_PINHOLE, intr, nullptr, depth_dev, color_dev, T_world_cam,
+                       cuda_stream);
 }
 
 tsdf_status integrate_lidar(tsdf_map* map, const float* range_dev, const tsdf_lidar* intr,
                             const double T_world_lidar[16], void* cuda_stream) {
-  return integrate_one(map, TSDF_SENSOR_LIDAR, nullptr, intr, range_dev, T_world_lidar, cuda_stream);
+  return integrate_one(map, TSDF_SENSOR_LIDAR, nullptr, intr, range_dev, nullptr, T_world_lidar,
+                       cuda_stream);
 }
 
 tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_frame_desc* frames,
@@ -422,7 +450,7 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
     const tsdf_frame_desc& fd = frames[f];
     if (fd.map < 0 || fd.map >= n_maps) return TSDF_ERR_ARG;
     tsdf_status st = fill_frame(maps[fd.map], fd.map, fd.kind, &fd.pinhole, &fd.lidar,
-                                fd.depth_dev, fd.T_world_sensor, fr[f]);
+                                fd.depth_dev, fd.color_dev, fd.T_world_sensor, fr[f]);
     if (st != TSDF_OK) return st;
   }
   // the params block is large; keep it off the stack
@@ -479,8 +507,20 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
 tsdf_status query_voxels(const tsdf_map* map, const float* pts_dev, int64_t n, float* dist_dev,
                          float* weight_dev, void* cuda_stream) {
   if (!map || n < 0 || (n > 0 && (!pts_dev || !dist_dev || !weight_dev))) return TSDF_ERR_ARG;
+  if (map->storage == gbt::kStorageColor) return TSDF_ERR_ARG;
   if (!on_device(map)) return TSDF_ERR_STATE;
   if (gbt::launch_query(map->dev, pts_dev, n, dist_dev, weight_dev, (cudaStream_t)cuda_stream) !=
+      cudaSuccess)
+    return cuda_fail();
+  return TSDF_OK;
+}
+
+tsdf_status query_color(const tsdf_map* map, const float* pts_dev, int64_t n, float* rgb_dev,
+                        float* weight_dev, void* cuda_stream) {
+  if (!map || n < 0 || (n > 0 && (!pts_dev || !rgb_dev || !weight_dev))) return TSDF_ERR_ARG;
+  if (map->storage != gbt::kStorageColor) return TSDF_ERR_ARG;
+  if (!on_device(map)) return TSDF_ERR_STATE;
+  if (gbt::launch_query_color(map->dev, pts_dev, n, rgb_dev, weight_dev, (cudaStream_t)cuda_stream) !=
       cudaSuccess)
     return cuda_fail();
   return TSDF_OK;
@@ -549,8 +589,12 @@ tsdf_status map_kernel_times(tsdf_map* map, double out_ms[2], int64_t* calls) {
   return TSDF_OK;
 }
 
-tsdf_status map_export(const tsdf_map* map, int32_t* keys_host, float* dist_host,
-                       float* weight_host, int64_t n) {
+namespace {
+
+// Shared body of map_export and map_export_color: rgb_host is used only for
+// colour maps, dist_host only for the others.
+tsdf_status export_blocks(const tsdf_map* map, int32_t* keys_host, float* dist_host, float* rgb_host,
+                          float* weight_host, int64_t n) {
   if (!map || !keys_host) return TSDF_ERR_ARG;
   int64_t nb = 0;
   tsdf_status st = map_num_blocks(map, &nb);
@@ -561,9 +605,9 @@ tsdf_status map_export(const tsdf_map* map, int32_t* keys_host, float* dist_host
   if (cudaMemcpy(bk.data(), map->dev.block_keys, sizeof(unsigned long long) * nb,
                  cudaMemcpyDeviceToHost) != cudaSuccess)
     return cuda_fail();
-  const size_t voxel_bytes = map->storage == TSDF_STORAGE_FP32 ? 8 : 4;
+  const size_t voxel_bytes = voxel_size_bytes(map->storage);
   std::vector<unsigned char> pool;
-  if (dist_host || weight_host) {
+  if (dist_host || rgb_host || weight_host) {
     pool.resize(voxel_bytes * gbt::kBlockVoxels * nb);
     if (cudaMemcpy(pool.data(), map->dev.pool, pool.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
       return cuda_fail();
@@ -583,7 +627,17 @@ tsdf_status map_export(const tsdf_map* map, int32_t* keys_host, float* dist_host
     if (pool.empty()) continue;
     for (int l = 0; l < gbt::kBlockVoxels; ++l) {
       float D, W;
-      if (map->storage == gbt::kStorageOcc) {
+      if (map->storage == gbt::kStorageColor) {
+        const float4 c = reinterpret_cast<const float4*>(pool.data())[(size_t)i * 512 + l];
+        if (rgb_host) {
+          float* out = rgb_host + ((size_t)r * 512 + l) * 3;
+          out[0] = c.x;
+          out[1] = c.y;
+          out[2] = c.z;
+        }
+        D = 0.0f;
+        W = c.w;
+      } else if (map->storage == gbt::kStorageOcc) {
         D = reinterpret_cast<const float*>(pool.data())[(size_t)i * 512 + l];
         W = 0.0f;
       } else if (map->storage == TSDF_STORAGE_FP16) {
@@ -600,6 +654,19 @@ tsdf_status map_export(const tsdf_map* map, int32_t* keys_host, float* dist_host
     }
   }
   return TSDF_OK;
+}
+
+}  // namespace
+
+tsdf_status map_export(const tsdf_map* map, int32_t* keys_host, float* dist_host,
+                       float* weight_host, int64_t n) {
+  return export_blocks(map, keys_host, dist_host, nullptr, weight_host, n);
+}
+
+tsdf_status map_export_color(const tsdf_map* map, int32_t* keys_host, float* rgb_host,
+                             float* weight_host, int64_t n) {
+  if (!map || map->storage != gbt::kStorageColor) return TSDF_ERR_ARG;
+  return export_blocks(map, keys_host, nullptr, rgb_host, weight_host, n);
 }
 
 tsdf_status map_reset(tsdf_map* map, void* cuda_stream) {

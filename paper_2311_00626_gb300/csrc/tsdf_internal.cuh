@@ -40,9 +40,9 @@ enum : int {
 enum : unsigned long long { kStPoolFull = 1, kStHashFull = 2, kStListFull = 4, kStTimeout = 8 };
 
 enum : int { kSensorPinhole = 0, kSensorLidar = 1 };
-// Voxel storage: TSDF {D, W} as FP32 or FP16 (D / tau), or occupancy
-// log-odds as one FP32 value.
-enum : int { kStorageF32 = 0, kStorageF16 = 1, kStorageOcc = 2 };
+// Voxel storage: TSDF {D, W} as FP32 or FP16 (D / tau), occupancy
+// log-odds as one FP32 value, or colour {r, g, b, W} as four FP32 values.
+enum : int { kStorageF32 = 0, kStorageF16 = 1, kStorageOcc = 2, kStorageColor = 3 };
 
 // Device view of one map.  The work list holds the hash slots met by the
 // frames of the batch in flight; the integration launch consumes it and its
@@ -83,6 +83,7 @@ struct MapDev {
 struct FrameDev {
   int32_t kind, map, width, height;
   const float* depth;
+  const uint32_t* rgba;  // colour layer: registered colour image (r in the low byte)
   const float* tab;      // LiDAR: cos/sin of beam azimuths [2*n_az], then polar [2*n_el]
   float fu, fv, cu, cv;  // pinhole
   float theta_start, phi_start, alpha, beta, min_range, max_range;  // LiDAR
@@ -128,6 +129,8 @@ template <int NF, int NM>
 cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile_h, cudaStream_t s);
 template <int NF, int NM>
 cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStream_t s);
+cudaError_t launch_query_color(const MapDev& m, const float* pts, int64_t n, float* rgb, float* weight,
+                               cudaStream_t s);
 cudaError_t launch_query(const MapDev& m, const float* pts, int64_t n, float* dist, float* weight,
                          cudaStream_t s);
 cudaError_t launch_reset(const MapDev& m, uint32_t cap, cudaStream_t s);

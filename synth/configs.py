@@ -20,7 +20,7 @@ from . import (BOX, PLANE, SPHERE, outdoor_scene, prim, render_lidar, render_pin
 
 __all__ = ["Frame", "Workload", "pinhole", "lidar64", "config_tiny", "config_room",
            "config_rig", "config_serving_maps", "serving_arrivals", "render_frame",
-           "cached"]
+           "color_image", "cached"]
 
 _CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), ".synth_cache")
 
@@ -64,6 +64,31 @@ def render_frame(prims, sensor, T, noise: dict, seed: int, frame: int) -> np.nda
     return render_lidar(prims, T, sensor["n_az"], sensor["n_el"], sensor["theta_start"],
                         sensor["phi_start"], sensor["el_fov"], sensor["min_range"],
                         sensor["max_range"], noise.get("sigma", 0.0), seed, frame)
+
+
+def color_image(sensor, T, depth, seed: int, frame: int) -> np.ndarray:
+    """Colour image registered to a pinhole depth image: uint32 [H, W], r in
+    the low byte, then g, b (top byte 0).  The colour is a smooth procedural
+    texture of the world point the pixel sees (back-projected from its
+    depth), so views of one surface agree, plus a seeded per-pixel jitter of
+    up to +-3 levels per channel (sensor noise); pixels without a valid
+    depth get a random colour."""
+    H, W = sensor["height"], sensor["width"]
+    jj, ii = np.meshgrid(np.arange(H, dtype=np.float64), np.arange(W, dtype=np.float64),
+                         indexing="ij")
+    d = depth.astype(np.float64)
+    ok = np.isfinite(d) & (d > 0)
+    d = np.where(ok, d, 1.0)
+    pc = np.stack([(ii - sensor["cu"]) / sensor["fu"] * d, (jj - sensor["cv"]) / sensor["fv"] * d, d])
+    pw = np.einsum("ij,jhw->ihw", T[:3, :3], pc) + T[:3, 3, None, None]
+    x, y, z = pw
+    tex = np.stack([128 + 100 * np.sin(3.1 * x + 1.3 * z), 128 + 100 * np.sin(2.3 * y - 0.7 * x),
+                    128 + 100 * np.cos(1.7 * z + 2.9 * y)])
+    rng = np.random.default_rng([seed, frame, 7])
+    tex = np.rint(tex) + rng.integers(-3, 4, size=tex.shape)
+    tex = np.where(ok[None], tex, rng.integers(0, 256, size=tex.shape))
+    c = np.clip(tex, 0, 255).astype(np.uint32)
+    return (c[0] | (c[1] << 8) | (c[2] << 16)).astype(np.uint32)
 
 
 def cached(key: str, fn):
