@@ -50,6 +50,8 @@ def _load():
             lib.orc_set_lidar_sampling.argtypes = [P, I, F]
             lib.orc_set_occupancy.argtypes = [P, F, F]
             lib.orc_set_weighting.argtypes = [P, I, F]
+            lib.orc_decay_occupancy.argtypes = [P, F, F]
+            lib.orc_decay_occupancy.restype = I
             lib.orc_integrate_pinhole.argtypes = [P, P, I, I, F, F, F, F, P]
             lib.orc_integrate_pinhole.restype = I
             lib.orc_integrate_color.argtypes = [P, P, P, I, I, F, F, F, F, P]
@@ -110,6 +112,12 @@ class OracleMap:
     def set_occupancy(self, l_occ: float, l_free: float):
         """Occupancy layer: D becomes the log-odds, W the number of updates."""
         self._lib.orc_set_occupancy(self._h, l_occ, l_free)
+
+    def decay_occupancy(self, decay_occ: float, decay_free: float):
+        """One decay step: occupied log-odds drop by decay_occ, free ones rise
+        by decay_free, neither crossing 0."""
+        if self._lib.orc_decay_occupancy(self._h, decay_occ, decay_free) != 0:
+            raise RuntimeError("oracle decay_occupancy failed")
 
     def integrate(self, sensor: dict, T: np.ndarray, depth: np.ndarray):
         depth = np.ascontiguousarray(depth, np.float32)

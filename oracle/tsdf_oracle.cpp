@@ -20,7 +20,9 @@
  *     weights added up to max_weight (Sec. IV-B);
  *   - occupancy layer (Sec. IV-B, second functor), optional: the same voxels
  *     instead add a constant log-odds, negative in front of the surface
- *     (d_p > 0), positive otherwise.
+ *     (d_p > 0), positive otherwise; a decay step (Sec. VI: dynamic content
+ *     of an occupancy layer fades over time) moves every voxel's log-odds
+ *     toward 0 by a fixed amount without crossing 0.
  *
  * Storage: std::unordered_map from integer block coordinates to a block of
  * 8x8x8 voxels holding D (double) and W (double), voxel index
@@ -294,6 +296,14 @@ inline void occupancy_update(double& L, double& N, bool in_front, double l_occ, 
   N += 1.0;
 }
 
+/* Occupancy decay (Sec. VI, the paper gives no rule): log-odds above 0
+ * (occupied) drop by decay_occ, log-odds below 0 (free) rise by decay_free,
+ * neither crossing 0, so every voxel drifts back to the prior p = 0.5. */
+inline void occupancy_decay(double& L, double decay_occ, double decay_free) {
+  if (L > 0.0) L = std::max(L - decay_occ, 0.0);
+  else if (L < 0.0) L = std::min(L + decay_free, 0.0);
+}
+
 }  // namespace
 
 extern "C" {
@@ -329,6 +339,17 @@ void orc_set_occupancy(void* h, float l_occ, float l_free) {
   m->occupancy = 1;
   m->l_occ = (double)l_occ;
   m->l_free = (double)l_free;
+}
+
+/* One decay step of an occupancy layer over every allocated voxel (the
+ * update counts are kept).  Returns -1 if the layer is not an occupancy
+ * layer or a step is negative. */
+int32_t orc_decay_occupancy(void* h, float decay_occ, float decay_free) {
+  auto* m = static_cast<Oracle*>(h);
+  if (!m->occupancy || !(decay_occ >= 0.0f) || !(decay_free >= 0.0f)) return -1;
+  for (auto& kv : m->blocks)
+    for (int l = 0; l < 512; ++l) occupancy_decay(kv.second->D[l], decay_occ, decay_free);
+  return 0;
 }
 
 /* LiDAR sampling: nearest != 0 selects nearest-cell sampling (a test mode);

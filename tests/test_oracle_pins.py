@@ -456,6 +456,45 @@ def test_occupancy_plane_closed_form():
     assert mixed.sum() > 0
 
 
+def _decayed(L, k, d_occ, d_free):
+    return np.where(L > 0, np.maximum(L - k * d_occ, 0.0), np.where(L < 0, np.minimum(L + k * d_free, 0.0), 0.0))
+
+
+def test_occupancy_decay_closed_form():
+    """Occupancy decay (Sec. VI: dynamic content of an occupancy layer fades):
+    after the two-plane sequence of the closed-form test above, k decay
+    steps move occupied log-odds down by k * d_occ and free ones up by
+    k * d_free, neither crossing 0; update counts are kept.  Checked after 3
+    steps (no voxel reaches 0) and after 3 + 40 (every voxel at 0)."""
+    cam = synth.pinhole(64, 48, 50.0, 32.0, 24.0)
+    T = np.eye(4)
+    imgs = [synth.render_pinhole(scene(prim(PLANE, 0, 0, 1, z)), T, cam["fu"], cam["fv"],
+                                 cam["cu"], cam["cv"], 64, 48) for z in (2.0, 2.12)]
+    m = oracle.OracleMap(0.05)
+    m.set_occupancy(L_OCC, L_FREE)
+    for img in [imgs[0]] * 7 + [imgs[1]] * 5:
+        m.integrate(cam, T, img)
+    _, L0, N0 = m.export()
+    d_occ, d_free = F32(0.3), F32(0.15)
+    for _ in range(3):
+        m.decay_occupancy(d_occ, d_free)
+    _, L3, N3 = m.export()
+    np.testing.assert_array_equal(N3, N0)
+    np.testing.assert_allclose(L3, _decayed(L0, 3, d_occ, d_free), rtol=0, atol=1e-12)
+    moved = np.abs(L0) > 1.0
+    assert (L0[moved] > 0).any() and (L0[moved] < 0).any()
+    assert np.all(np.sign(L3[moved]) == np.sign(L0[moved]))  # nothing crossed 0 yet
+    for _ in range(40):
+        m.decay_occupancy(d_occ, d_free)
+    _, L43, _ = m.export()
+    assert np.all(L43 == 0.0)
+    with pytest.raises(RuntimeError):
+        m.decay_occupancy(-1.0, 0.0)
+    t = oracle.OracleMap(0.05)
+    with pytest.raises(RuntimeError):  # a TSDF layer has no decay
+        t.decay_occupancy(0.1, 0.1)
+
+
 def test_occupancy_lidar_sphere():
     """Inside a sphere of radius 10 m: voxels with |p| < 10 are free, those
     within tau outside it occupied, one observation each."""
