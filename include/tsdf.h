@@ -265,6 +265,18 @@ tsdf_status map_export(const tsdf_map* map, int32_t* keys_host, float* dist_host
 tsdf_status map_export_color(const tsdf_map* map, int32_t* keys_host, float* rgb_host,
                              float* weight_host, int64_t n);
 
+/*
+ * map_decay_occupancy — one decay step of an occupancy layer (Sec. VI: the
+ * dynamic part of a scene, kept in its own occupancy layer, fades over
+ * time; the paper gives no rule): every allocated voxel's log-odds moves
+ * toward 0 (probability 1/2), occupied values (> 0) by decay_occ, free
+ * values (< 0) by decay_free, neither crossing 0.  Blocks stay allocated.
+ * TSDF_ERR_ARG for another layer or a negative or non-finite step.  Async
+ * on cuda_stream.
+ */
+tsdf_status map_decay_occupancy(tsdf_map* map, float decay_occ, float decay_free,
+                                void* cuda_stream);
+
 /* map_reset — drop every block (keeps the allocation), enqueued on
  * cuda_stream; clears the sticky status. */
 tsdf_status map_reset(tsdf_map* map, void* cuda_stream);

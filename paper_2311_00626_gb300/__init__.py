@@ -23,7 +23,7 @@ __all__ = ["TsdfError", "Pinhole", "Lidar", "MapOpts", "FrameDesc", "TsdfMap", "
            "map_export", "map_reset", "map_destroy", "map_timing", "map_kernel_times",
            "MapBuffers", "integrate_depth_static", "STATIC_MAX_BLOCKS", "LAYER_TSDF",
            "LAYER_OCCUPANCY", "LAYER_COLOR", "STORAGE_FP32", "STORAGE_FP16",
-           "integrate_color", "query_color", "map_export_color",
+           "integrate_color", "query_color", "map_export_color", "map_decay_occupancy",
            "SENSOR_PINHOLE", "SENSOR_LIDAR", "EXPORTED_SYMBOLS"]
 
 STORAGE_FP32, STORAGE_FP16 = 0, 1
@@ -37,7 +37,7 @@ EXPORTED_SYMBOLS = ["map_create", "map_create_ex", "integrate_depth", "integrate
                     "integrate_batch", "query_voxels", "map_sync", "map_num_blocks", "map_stats",
                     "map_export", "map_reset", "map_destroy", "map_timing", "map_kernel_times",
                     "integrate_depth_static", "integrate_color", "query_color",
-                    "map_export_color"]
+                    "map_export_color", "map_decay_occupancy"]
 
 
 class TsdfError(RuntimeError):
@@ -116,6 +116,7 @@ def lib():
                 "integrate_color": ([P, P, P, ctypes.POINTER(Pinhole), P, P], I),
                 "query_color": ([P, P, L64, P, P, P], I),
                 "map_export_color": ([P, P, P, P, L64], I),
+                "map_decay_occupancy": ([P, F, F, P], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -272,6 +273,11 @@ def map_export_color(m: int):
     return keys, rgb, W
 
 
+def map_decay_occupancy(m: int, decay_occ: float, decay_free: float, stream=None):
+    _check(lib().map_decay_occupancy(m, decay_occ, decay_free, _stream(stream)),
+           "map_decay_occupancy")
+
+
 def map_reset(m: int, stream=None):
     _check(lib().map_reset(m, _stream(stream)), "map_reset")
 
@@ -337,6 +343,9 @@ class TsdfMap:
 
     def query_color(self, pts, rgb, weight, stream=None):
         query_color(self.handle, pts, rgb, weight, stream)
+
+    def decay(self, decay_occ: float, decay_free: float, stream=None):
+        map_decay_occupancy(self.handle, decay_occ, decay_free, stream)
 
     def reset(self, stream=None):
         map_reset(self.handle, stream)

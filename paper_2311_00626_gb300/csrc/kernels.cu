@@ -1,19 +1,23 @@
 // CUDA kernels of the GB300 TSDF library (sm_103a).
 //
-//  band_alloc_kernel  Sec. IV-B first step: every valid pixel's ray segment
-//                     inside the truncation band is walked through the block
-//                     grid (Amanatides & Woo traversal); lanes of a warp that
-//                     reach the same block are merged with match.any, the
-//                     leader inserts it into the open-addressing hash
-//                     (atomicCAS on the packed key), assigns a pool block if
-//                     new, and sets its frame bit; the first frame bit on a
-//                     block appends it to the batch work list.
-//  integrate_kernel   Sec. IV-B second step (Eq. 1-3 and the TSDF update
-//                     functor): one CTA per work-list block, 4 voxels per
-//                     thread held in registers across every frame of the
-//                     batch that met the block, one coalesced 16-byte read
-//                     and write per thread and frame batch.
-//  query_kernel       point -> voxel lookup through the hash.
+//  band_alloc_kernel  Sec. IV-B first step: one CTA per pixel tile; every
+//                     valid pixel's ray segment inside the truncation band is
+//                     walked through the block grid (Amanatides & Woo
+//                     traversal) and its blocks recorded in a CTA-local set
+//                     in shared memory; the tile's distinct blocks are then
+//                     claimed in the open-addressing hash (atomicCAS on the
+//                     packed key), given a pool block if new, and get the
+//                     frame's bit; the first bit on a block appends it to
+//                     the batch work list.
+//  integrate_kernel   Sec. IV-B second step (Eq. 1-3 and the update
+//                     functors: TSDF, occupancy, colour): persistent CTAs
+//                     take work-list blocks, 4 voxels per thread held in
+//                     registers across every frame of the batch that met the
+//                     block, one coalesced read and write per block and
+//                     batch.
+//  query_kernel,      point -> voxel lookup through the hash.
+//  query_color_kernel
+//  decay_kernel       occupancy decay over every allocated block (Sec. VI).
 //
 // Discrete decisions use explicit round-to-nearest intrinsics in a fixed
 // order (no contraction) so that they are reproducible on a CPU.
@@ -95,7 +99,7 @@ constexpr uint32_t kEmptyRel = 0xFFFFFFFFu;
 struct Walk32 {
   uint32_t key;
   uint32_t kx, ky, kz;  // key change of one step along each axis
-  float bx, by, bz;     // next boundary per axis
+  float bx, by, bz;     // next boundary per axis (+inf for an axis the ray does not cross)
   float fx, fy, fz;     // step per axis (+1, -1, 0)
   float ix, iy, iz;
   float tx, ty, tz;
@@ -103,18 +107,17 @@ struct Walk32 {
   float s1;
   int n;
 
+  // t of an axis is always (b - o) * inv; an axis with zero direction has
+  // b = +inf and inv = 1, so its t is +inf.
   __device__ __forceinline__ void axis(float d, float fl, float o, uint32_t unit, float& f,
                                        uint32_t& k, float& inv, float& b, float& t) {
     const bool pos = d > 0.0f, neg = d < 0.0f;
     f = pos ? 1.0f : (neg ? -1.0f : 0.0f);
     k = pos ? unit : (neg ? 0u - unit : 0u);
-    inv = (pos || neg) ? __frcp_rn(d) : 0.0f;
-    b = pos ? fl + 1.0f : fl;
-    t = (pos || neg) ? __fmul_rn(__fsub_rn(b, o), inv) : __int_as_float(0x7f800000);
+    inv = (pos || neg) ? __frcp_rn(d) : 1.0f;
+    b = pos ? fl + 1.0f : (neg ? fl : __int_as_float(0x7f800000));
+    t = __fmul_rn(__fsub_rn(b, o), inv);
   }
-  // start cell = floor(o + s0 dir); px, py, pz is that point.  The key
-  // counts cells from `base` (anchor-relative); only the key's origin
-  // depends on it, not the walk's arithmetic.
   __device__ __forceinline__ void start(float px, float py, float pz, float ox_, float oy_, float oz_,
                                         float dx, float dy, float dz, float s1_, int bx0, int by0,
                                         int bz0, uint32_t flag) {
@@ -132,23 +135,19 @@ struct Walk32 {
   }
   __device__ __forceinline__ bool next() {
     const bool sy_ = ty < tx;
-    const float t01 = sy_ ? ty : tx;
+    const float t01 = fminf(tx, ty);
     const bool sz_ = tz < t01;
-    const float t = sz_ ? tz : t01;
+    const float t = fminf(t01, tz);
     if (!(t <= s1) || n == kMaxCells) return false;
-    // branch-free: one axis advances, chosen by selects
     const bool sx_ = !sz_ && !sy_, syy = !sz_ && sy_;
     key += sz_ ? kz : (sy_ ? ky : kx);
-    bx = sx_ ? bx + fx : bx;
-    by = syy ? by + fy : by;
-    bz = sz_ ? bz + fz : bz;
-    const float bsel = sz_ ? bz : (sy_ ? by : bx);
-    const float osel = sz_ ? oz : (sy_ ? oy : ox);
-    const float isel = sz_ ? iz : (sy_ ? iy : ix);
-    const float tnew = __fmul_rn(__fsub_rn(bsel, osel), isel);
-    tx = sx_ ? tnew : tx;
-    ty = syy ? tnew : ty;
-    tz = sz_ ? tnew : tz;
+    bx += sx_ ? fx : 0.0f;
+    by += syy ? fy : 0.0f;
+    bz += sz_ ? fz : 0.0f;
+    // recomputing the unchanged axes reproduces their t exactly
+    tx = __fmul_rn(__fsub_rn(bx, ox), ix);
+    ty = __fmul_rn(__fsub_rn(by, oy), iy);
+    tz = __fmul_rn(__fsub_rn(bz, oz), iz);
     ++n;
     return true;
   }
@@ -193,13 +192,14 @@ __device__ __noinline__ bool set_insert_slow(uint32_t* set, uint32_t key, uint32
 // direction in anchor-relative block units per unit of depth (camera) or
 // range (LiDAR) and the band [max(d - tau, 0), d + tau].  False if the pixel
 // is outside the image or its depth is invalid.
+template <bool PINHOLE_ONLY>
 __device__ __forceinline__ bool pixel_segment(const FrameDev& F, const MapDev& m,
                                               const float* s_ray, int i, int j, int lane, int ty,
                                               float d, float& dx, float& dy, float& dz, float& s0,
                                               float& s1) {
   if (i >= F.width || j >= F.height) return false;
   bool valid;
-  if (F.kind == kSensorPinhole) {
+  if (PINHOLE_ONLY || F.kind == kSensorPinhole) {
     valid = d > 0.0f && d <= FLT_MAX;
     const float rx = s_ray[lane], ry = s_ray[kTileW + ty];
     dx = __fmaf_rn(F.M[0], rx, __fmaf_rn(F.M[1], ry, F.M[2]));
@@ -223,8 +223,9 @@ __device__ __forceinline__ bool pixel_segment(const FrameDev& F, const MapDev& m
 // band segments of one pixel row at a time and records the blocks met in a
 // CTA-local set; then the tile's distinct blocks are claimed in the global
 // hash.  Segments that start far from the sensor's block count cells from
-// their own start cell and claim their blocks directly.
-template <int NF, int NM, int TH>
+// their own start cell and claim their blocks directly.  PINHOLE_ONLY: every
+// frame of the batch is a pinhole camera (the LiDAR code is left out).
+template <int NF, int NM, int TH, bool PINHOLE_ONLY>
 __global__ void __launch_bounds__(kAllocThreads)
     band_alloc_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
   constexpr int kRows = TH * kTileW / kAllocThreads;  // pixel rows per thread
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(kAllocThreads)
     const int i = x0 + lane, j = y0 + wy + q * (kAllocThreads / kTileW);
     dep[q] = (i < F.width && j < F.height) ? __ldg(F.depth + (size_t)j * F.width + i) : 0.0f;
   }
-  if (F.kind == kSensorPinhole) {
+  if (PINHOLE_ONLY || F.kind == kSensorPinhole) {
     if (threadIdx.x < kTileW)
       s_ray[threadIdx.x] = __fdiv_rn(__fsub_rn((float)(x0 + (int)threadIdx.x), F.cu), F.fu);
     else if (threadIdx.x < kTileW + TH)
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(kAllocThreads)
     wk.key = kEmptyRel;
     int b0x = 0, b0y = 0, b0z = 0;  // key origin of a far segment
     float dx, dy, dz, s0, s1;
-    if (pixel_segment(F, m, s_ray, x0 + lane, y0 + ty, lane, ty, dep[q], dx, dy, dz, s0, s1)) {
+    if (pixel_segment<PINHOLE_ONLY>(F, m, s_ray, x0 + lane, y0 + ty, lane, ty, dep[q], dx, dy, dz, s0, s1)) {
       const float px = __fmaf_rn(s0, dx, F.o[0]), py = __fmaf_rn(s0, dy, F.o[1]),
                   pz = __fmaf_rn(s0, dz, F.o[2]);
       if (fabsf(px) < kRelStart && fabsf(py) < kRelStart && fabsf(pz) < kRelStart) {
@@ -630,7 +631,7 @@ __device__ __forceinline__ void fuse_any(const FrameDev& F, const MapDev& m, con
   }
 }
 
-template <int NF, int NM, int STORAGE>
+template <int NF, int NM, int STORAGE, bool PINHOLE_ONLY>
 __global__ void __launch_bounds__(kIntegrateThreads)
     integrate_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
   __shared__ uint32_t s_begin[NM + 1];
@@ -695,7 +696,7 @@ __global__ void __launch_bounds__(kIntegrateThreads)
           fq[q] = -1;
           if (go && bits) {
             const int f = __ffs(bits) - 1;
-            if (p.fr[f].kind == kSensorPinhole) {
+            if (PINHOLE_ONLY || p.fr[f].kind == kSensorPinhole) {
               fq[q] = f;
               ++nq;
               bits &= bits - 1u;
@@ -711,7 +712,7 @@ __global__ void __launch_bounds__(kIntegrateThreads)
             fuse_pinhole<1, STORAGE>(p, fq1, m, vr, D, W, G, B, my_upd);
           }
         }
-        else {
+        else if (!PINHOLE_ONLY) {
           const int f = __ffs(bits) - 1;  // a LiDAR frame
           bits &= bits - 1u;
           fuse_any<STORAGE>(p.fr[f], m, vr, D, W, my_upd);
@@ -807,6 +808,26 @@ __global__ void query_color_kernel(const MapDev m, const float* __restrict__ pts
   weight[i] = out.w;
 }
 
+// Occupancy decay over every allocated block: log-odds above 0 drop by
+// d_occ, below 0 rise by d_free, neither crossing 0.  The pool's first
+// min(blocks, max_blocks) blocks are exactly the allocated ones; a thread
+// handles four voxels (one 16-byte word) per step of a grid-stride loop.
+__global__ void decay_kernel(const MapDev m, float d_occ, float d_free) {
+  const unsigned long long nb =
+      min((unsigned long long)m.max_blocks, __ldcg(m.counters + kCntBlocks));
+  const size_t n4 = (size_t)nb * 128;
+  float4* pool = reinterpret_cast<float4*>(m.pool);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (size_t)gridDim.x * blockDim.x) {
+    float4 l = pool[i];
+    float* c = &l.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      c[k] = c[k] > 0.0f ? fmaxf(c[k] - d_occ, 0.0f) : (c[k] < 0.0f ? fminf(c[k] + d_free, 0.0f) : c[k]);
+    pool[i] = l;
+  }
+}
+
 __global__ void reset_kernel(const MapDev m, uint32_t cap) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) {
     m.keys[i] = kEmptyKey;
@@ -819,27 +840,50 @@ __global__ void reset_kernel(const MapDev m, uint32_t cap) {
 
 }  // namespace
 
+// True when every frame of the batch is a pinhole camera: the kernels are
+// then launched without their LiDAR code (smaller, fewer branches).
+template <int NF, int NM>
+bool pinhole_only(const BatchParams<NF, NM>& p) {
+  for (int f = 0; f < p.n_frames; ++f)
+    if (p.fr[f].kind != kSensorPinhole) return false;
+  return true;
+}
+
 template <int NF, int NM>
 cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile_h, cudaStream_t s) {
   if (n_ctas <= 0) return cudaSuccess;
-  if (tile_h == kTileHBig)
-    band_alloc_kernel<NF, NM, kTileHBig><<<n_ctas, kAllocThreads, 0, s>>>(p);
+  const bool ph = pinhole_only(p);
+  if (tile_h == kTileHBig && ph)
+    band_alloc_kernel<NF, NM, kTileHBig, true><<<n_ctas, kAllocThreads, 0, s>>>(p);
+  else if (tile_h == kTileHBig)
+    band_alloc_kernel<NF, NM, kTileHBig, false><<<n_ctas, kAllocThreads, 0, s>>>(p);
+  else if (ph)
+    band_alloc_kernel<NF, NM, kTileHSmall, true><<<n_ctas, kAllocThreads, 0, s>>>(p);
   else
-    band_alloc_kernel<NF, NM, kTileHSmall><<<n_ctas, kAllocThreads, 0, s>>>(p);
+    band_alloc_kernel<NF, NM, kTileHSmall, false><<<n_ctas, kAllocThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 
 template <int NF, int NM>
 cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStream_t s) {
   // all maps of a batch share one storage type (checked by the host API)
-  if (p.maps[0].storage == kStorageColor)
-    integrate_kernel<NF, NM, kStorageColor><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
-  else if (p.maps[0].storage == kStorageOcc)
-    integrate_kernel<NF, NM, kStorageOcc><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
-  else if (p.maps[0].storage == kStorageF16)
-    integrate_kernel<NF, NM, kStorageF16><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+  // colour maps take pinhole frames only (checked by the host API)
+  const bool ph = pinhole_only(p);
+  const int st = p.maps[0].storage;
+  if (st == kStorageColor)
+    integrate_kernel<NF, NM, kStorageColor, true><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+  else if (st == kStorageOcc && ph)
+    integrate_kernel<NF, NM, kStorageOcc, true><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+  else if (st == kStorageOcc)
+    integrate_kernel<NF, NM, kStorageOcc, false><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+  else if (st == kStorageF16 && ph)
+    integrate_kernel<NF, NM, kStorageF16, true><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+  else if (st == kStorageF16)
+    integrate_kernel<NF, NM, kStorageF16, false><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+  else if (ph)
+    integrate_kernel<NF, NM, kStorageF32, true><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
   else
-    integrate_kernel<NF, NM, kStorageF32><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+    integrate_kernel<NF, NM, kStorageF32, false><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -873,6 +917,14 @@ cudaError_t launch_query_color(const MapDev& m, const float* pts, int64_t n, flo
   return cudaGetLastError();
 }
 
+cudaError_t launch_decay(const MapDev& m, float d_occ, float d_free, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  decay_kernel<<<sms * 8, 256, 0, s>>>(m, d_occ, d_free);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reset(const MapDev& m, uint32_t cap, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -886,16 +938,16 @@ int integrate_ctas_per_sm(int storage) {
   cudaError_t e;
   if (storage == kStorageColor)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageColor>, kIntegrateThreads, 0);
+        &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageColor, true>, kIntegrateThreads, 0);
   else if (storage == kStorageOcc)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageOcc>, kIntegrateThreads, 0);
+        &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageOcc, false>, kIntegrateThreads, 0);
   else if (storage == kStorageF16)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageF16>, kIntegrateThreads, 0);
+        &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageF16, false>, kIntegrateThreads, 0);
   else
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageF32>, kIntegrateThreads, 0);
+        &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageF32, false>, kIntegrateThreads, 0);
   if (e != cudaSuccess || n <= 0) n = 4;
   return n;
 }

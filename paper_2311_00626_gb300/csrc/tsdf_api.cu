@@ -669,6 +669,17 @@ tsdf_status map_export_color(const tsdf_map* map, int32_t* keys_host, float* rgb
   return export_blocks(map, keys_host, nullptr, rgb_host, weight_host, n);
 }
 
+tsdf_status map_decay_occupancy(tsdf_map* map, float decay_occ, float decay_free,
+                                void* cuda_stream) {
+  if (!map || map->storage != gbt::kStorageOcc || !(decay_occ >= 0.0f) || !(decay_free >= 0.0f) ||
+      !std::isfinite(decay_occ) || !std::isfinite(decay_free))
+    return TSDF_ERR_ARG;
+  if (!on_device(map)) return TSDF_ERR_STATE;
+  if (gbt::launch_decay(map->dev, decay_occ, decay_free, (cudaStream_t)cuda_stream) != cudaSuccess)
+    return cuda_fail();
+  return TSDF_OK;
+}
+
 tsdf_status map_reset(tsdf_map* map, void* cuda_stream) {
   if (!map) return TSDF_ERR_ARG;
   if (!on_device(map)) return TSDF_ERR_STATE;

@@ -134,6 +134,7 @@ cudaError_t launch_query_color(const MapDev& m, const float* pts, int64_t n, flo
 cudaError_t launch_query(const MapDev& m, const float* pts, int64_t n, float* dist, float* weight,
                          cudaStream_t s);
 cudaError_t launch_reset(const MapDev& m, uint32_t cap, cudaStream_t s);
+cudaError_t launch_decay(const MapDev& m, float d_occ, float d_free, cudaStream_t s);
 int integrate_ctas_per_sm(int storage);
 
 }  // namespace gbt

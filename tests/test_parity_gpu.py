@@ -375,6 +375,43 @@ def test_occupancy_lidar():
     _occ_parity("occ_lidar", frames, 0.05)
 
 
+def test_occupancy_decay_interleaved():
+    """Occupancy decay (Sec. VI) interleaved with integration: 10 room frames,
+    2 decay steps, 10 more frames, 3 steps, against the oracle doing the
+    same; the log-odds carry the FP32 error of a running sum of 25 terms."""
+    import oracle
+    import paper_2311_00626_gb300 as gt
+    r = synth.config_room(n_frames=300)
+    frames = r.frames[100:120]
+    d_occ, d_free = float(np.float32(0.3)), float(np.float32(0.15))
+    om = oracle.OracleMap(r.voxel_size)
+    om.set_occupancy(*OCC)
+    gm = gt.TsdfMap(r.voxel_size, layer=gt.LAYER_OCCUPANCY, l_occ=OCC[0], l_free=OCC[1])
+    dev = [torch.from_numpy(np.ascontiguousarray(f.depth)).cuda() for f in frames]
+    for part, steps in ((slice(0, 10), 2), (slice(10, 20), 3)):
+        for f, d in zip(frames[part], dev[part]):
+            om.integrate(f.sensor, f.T, f.depth)
+            gm.integrate(f.sensor, f.T, d)
+        for _ in range(steps):
+            om.decay_occupancy(d_occ, d_free)
+            gm.decay(d_occ, d_free)
+    torch.cuda.synchronize()
+    assert gm.sync() == 0
+    st = compare_occupancy(gm.export(), om.export(), 25, 0.85, "occ_decay")
+    assert st["blocks"] > 1000
+    _record("occ_decay", st)
+    ok, oL, oN = om.export()
+    assert (oL > 0).any() and (oL < 0).any() and ((oL == 0) & (oN > 0)).any()
+    with pytest.raises(gt.TsdfError):
+        gm.decay(-0.1, 0.0)
+    t = gt.TsdfMap(r.voxel_size)
+    with pytest.raises(gt.TsdfError):  # not an occupancy layer
+        t.decay(0.1, 0.1)
+    t.close()
+    gm.close()
+    om.close()
+
+
 # ------------------------------------------------------ weighting functions
 
 @pytest.mark.parametrize("mode", [1, 2, 3])
