@@ -1,7 +1,8 @@
 """CPU oracle for projective TSDF integration — TEST INFRASTRUCTURE ONLY.
 
 A plain FP64 restatement of nvblox's frame integration (Sec. IV-B, Eq. 1-3)
-in ``tsdf_oracle.cpp``, loaded through ctypes.  Only the test suite, the
+in ``tsdf_oracle.cpp`` and of its incremental ESDF (Sec. IV-C) in
+``esdf_oracle.cpp``, loaded through ctypes.  Only the test suite, the
 package smoke check and the benchmark's CPU-baseline leg may import this
 module; the product path never does, and it shares no code with the CUDA
 path.  See the header of ``tsdf_oracle.cpp`` for the precision contract
@@ -17,18 +18,19 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "tsdf_oracle.cpp")
+_SRCS = [os.path.join(_HERE, "tsdf_oracle.cpp"), os.path.join(_HERE, "esdf_oracle.cpp")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile tsdf_oracle.cpp into liboracle.so (g++, FP contraction off)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+    """Compile the oracle sources into liboracle.so (g++, FP contraction off)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(p) for p in _SRCS)):
         return _LIB
     cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-           _SRC, "-o", _LIB + ".tmp"]
+           *_SRCS, "-o", _LIB + ".tmp"]
     try:
         subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -71,6 +73,16 @@ def _load():
             lib.orc_atan2_dec.restype = F
             lib.orc_dda.argtypes = [P, P, F, F, P]
             lib.orc_dda.restype = I
+            lib.esdf_orc_create.argtypes = [F, F, F, I]
+            lib.esdf_orc_create.restype = P
+            lib.esdf_orc_destroy.argtypes = [P]
+            lib.esdf_orc_update.argtypes = [P, P, P, P, L, P]
+            lib.esdf_orc_update.restype = L
+            lib.esdf_orc_num_blocks.argtypes = [P]
+            lib.esdf_orc_num_blocks.restype = L
+            lib.esdf_orc_export.argtypes = [P, P, P, L]
+            lib.esdf_orc_export.restype = L
+            lib.esdf_orc_counters.argtypes = [P, P]
             _lib = lib
             del D
     return _lib
@@ -197,3 +209,58 @@ def dda(o, direction, s0: float, s1: float) -> np.ndarray:
     cells = np.zeros((32, 3), np.int32)
     n = _load().orc_dda(_p(o), _p(direction), s0, s1, _p(cells))
     return cells[:n].copy()
+
+
+# ESDF state word (see esdf_oracle.cpp): 9-bit parent offsets, then flags
+ESDF_OBS, ESDF_SITE, ESDF_PAR, ESDF_INSIDE = 1 << 27, 1 << 28, 1 << 29, 1 << 30
+
+
+def esdf_offsets(states: np.ndarray) -> np.ndarray:
+    """int32 [..., 3] parent offsets of ESDF state words."""
+    s = states.astype(np.int64)
+    raw = np.stack([(s >> (9 * a)) & 511 for a in range(3)], -1)
+    return np.where(raw >= 256, raw - 512, raw).astype(np.int32)
+
+
+class EsdfOracle:
+    """Incremental ESDF over TSDF blocks (Sec. IV-C), integer parent offsets."""
+
+    def __init__(self, voxel_size: float, site_eps: float, min_weight: float, max_dist_vox: int):
+        self._lib = _load()
+        self._h = self._lib.esdf_orc_create(voxel_size, site_eps, min_weight, max_dist_vox)
+        if not self._h:
+            raise ValueError("bad ESDF parameters")
+
+    def close(self):
+        if self._h:
+            self._lib.esdf_orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, keys: np.ndarray, D: np.ndarray, W: np.ndarray, changed=None) -> int:
+        """keys int32 [n,3], D / W float32 [n,512] (the TSDF blocks), changed
+        bool [n] (default: all).  Returns the lowering iterations."""
+        keys = np.ascontiguousarray(keys, np.int32)
+        D = np.ascontiguousarray(D, np.float32)
+        W = np.ascontiguousarray(W, np.float32)
+        n = len(keys)
+        ch = np.ones(n, np.uint8) if changed is None else np.ascontiguousarray(changed, np.uint8)
+        return int(self._lib.esdf_orc_update(self._h, _p(keys), _p(D), _p(W), n, _p(ch)))
+
+    def export(self):
+        """(keys int32 [n,3] sorted by (x,y,z), states uint32 [n,512])."""
+        n = int(self._lib.esdf_orc_num_blocks(self._h))
+        keys = np.zeros((n, 3), np.int32)
+        st = np.zeros((n, 512), np.uint32)
+        assert self._lib.esdf_orc_export(self._h, _p(keys), _p(st), n) == n
+        return keys, st
+
+    def counters(self) -> dict:
+        out = np.zeros(4, np.int64)
+        self._lib.esdf_orc_counters(self._h, _p(out))
+        return dict(zip(["iterations", "swept", "pulled", "cleared"], (int(x) for x in out)))

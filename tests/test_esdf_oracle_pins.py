@@ -1,0 +1,166 @@
+"""Pins of the ESDF oracle (Sec. IV-C) against brute force and closed forms.
+
+The TSDF inputs are written directly from signed distance functions of
+planes and spheres (no integration involved), so the site set is known; the
+exact Euclidean distance transform over the observed voxels is computed by
+brute force (every voxel against every site) and is the reference.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ESDF_INSIDE, ESDF_OBS, ESDF_PAR, ESDF_SITE, esdf_offsets
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+V = np.float32(0.05)
+
+
+def tsdf_region(lo, hi, sdf, tau=4 * 0.05, observed=None):
+    """TSDF blocks lo <= key < hi (block coords) with D = clip(sdf(centre),
+    -tau, tau) and W = 1 (0 where observed(centre) is False)."""
+    keys = np.array([(x, y, z) for x in range(lo[0], hi[0]) for y in range(lo[1], hi[1])
+                     for z in range(lo[2], hi[2])], np.int32)
+    l = np.arange(512)
+    loc = np.stack([l % 8, (l // 8) % 8, l // 64], -1)
+    g = keys[:, None, :] * 8 + loc[None]
+    c = (g + 0.5) * float(V)
+    D = np.clip(sdf(c), -tau, tau).astype(np.float32)
+    W = np.ones_like(D)
+    if observed is not None:
+        W[~observed(c)] = 0.0
+    return keys, D, W, g
+
+
+def brute_edt2(g, site_mask, obs_mask, chunk=4096):
+    """Exact squared distance (voxels) from every voxel to the nearest site."""
+    sites = g[site_mask].astype(np.int64)
+    pts = g.reshape(-1, 3).astype(np.int64)
+    out = np.full(len(pts), np.iinfo(np.int64).max, np.int64)
+    for s in range(0, len(pts), chunk):
+        d = ((pts[s:s + chunk, None, :] - sites[None]) ** 2).sum(-1)
+        out[s:s + chunk] = d.min(1)
+    return out.reshape(g.shape[:-1])
+
+
+def run(keys, D, W, eps, max_dist, changed=None, e=None):
+    e = e or oracle.EsdfOracle(float(V), eps, 1e-4, max_dist)
+    it = e.update(keys, D, W, changed)
+    k, st = e.export()
+    order = np.lexsort((keys[:, 2], keys[:, 1], keys[:, 0]))
+    np.testing.assert_array_equal(k, keys[order])
+    return e, st, order, it
+
+
+def check_parents_are_sites(st, g_sorted, site_set):
+    par = (st & ESDF_PAR) != 0
+    pg = g_sorted + esdf_offsets(st)
+    for p in pg[par].reshape(-1, 3)[:: max(1, par.sum() // 20000)]:
+        assert tuple(p) in site_set
+
+
+def test_plane_equals_brute_force():
+    """Plane z = 0.43 m: every observed voxel's distance is its exact
+    distance (in voxels) to the nearest site, across block borders; the
+    side (inside = D < 0) follows the TSDF sign."""
+    eps = float(V)
+    keys, D, W, g = tsdf_region((0, 0, 0), (3, 3, 4), lambda c: c[..., 2] - 0.43)
+    e, st, order, it = run(keys, D, W, eps, 40)
+    site = np.abs(D) <= np.float32(eps)
+    exact = brute_edt2(g, site, W > 0)
+    d2 = (esdf_offsets(st) ** 2).sum(-1)
+    assert np.all((st & ESDF_PAR) != 0)
+    np.testing.assert_array_equal(d2, exact[order])
+    np.testing.assert_array_equal((st & ESDF_SITE) != 0, site[order])
+    np.testing.assert_array_equal((st & ESDF_INSIDE) != 0, (D < 0)[order])
+    assert d2.max() >= 20 ** 2 and it >= 3  # distances cross several blocks
+
+
+def test_sphere_close_to_brute_force():
+    """Sphere r = 0.52 m: parent propagation reaches every voxel, each parent
+    is a site and no distance is below the exact one.  Propagation keeps,
+    per voxel, one of the sites handed on by its six neighbours, so near a
+    curved surface it can miss the nearest site: a site one diagonal step
+    away (sqrt 2) that no axis neighbour carries is replaced by one two axis
+    steps away, an excess of 2 - sqrt 2.  The excess stays within that and
+    at least 93 % of the voxels are exact."""
+    eps = float(V)
+    ctr = np.array([0.83, 0.77, 0.91])
+    keys, D, W, g = tsdf_region((0, 0, 0), (4, 4, 4),
+                                lambda c: np.linalg.norm(c - ctr, axis=-1) - 0.52)
+    e, st, order, _ = run(keys, D, W, eps, 60)
+    site = np.abs(D) <= np.float32(eps)
+    exact = brute_edt2(g, site, W > 0)[order]
+    d2 = (esdf_offsets(st) ** 2).sum(-1)
+    assert np.all((st & ESDF_PAR) != 0)
+    assert np.all(d2 >= exact)
+    excess = np.sqrt(d2) - np.sqrt(exact)
+    assert excess.max() <= 2 - np.sqrt(2) + 1e-9
+    assert np.mean(d2 == exact) >= 0.93
+    check_parents_are_sites(st, g[order], set(map(tuple, g[site].reshape(-1, 3))))
+
+
+def test_max_distance():
+    """Voxels farther than max_dist from every site keep no parent; the rest
+    are exact (plane)."""
+    eps = float(V)
+    keys, D, W, g = tsdf_region((0, 0, 0), (2, 2, 4), lambda c: c[..., 2] - 0.43)
+    _, st, order, _ = run(keys, D, W, eps, 5)
+    exact = brute_edt2(g, np.abs(D) <= np.float32(eps), W > 0)[order]
+    par = (st & ESDF_PAR) != 0
+    np.testing.assert_array_equal(par, exact <= 25)
+    np.testing.assert_array_equal((esdf_offsets(st) ** 2).sum(-1)[par], exact[par])
+    assert np.all(st[~par] == ESDF_OBS) or np.all((st[~par] & ESDF_OBS) != 0)
+
+
+def test_incremental_move_equals_fresh():
+    """A plane at z = 0.43 m, then the part with x < 0.6 m moved to 0.97 m:
+    updating with only the changed blocks clears the children of the
+    vanished sites and gives the same distances and flags as computing the
+    second TSDF from scratch (a voxel may keep another parent at the same
+    distance: ties keep the parent found first); every parent is a current
+    site and no distance is below brute force."""
+    eps = float(V)
+    f1 = lambda c: c[..., 2] - 0.43  # noqa: E731
+    f2 = lambda c: np.where(c[..., 0] < 0.6, c[..., 2] - 0.97, c[..., 2] - 0.43)  # noqa: E731
+    keys, D1, W, g = tsdf_region((0, 0, 0), (3, 2, 4), f1)
+    _, D2, _, _ = tsdf_region((0, 0, 0), (3, 2, 4), f2)
+    changed = np.any(D1 != D2, axis=1)
+    assert 0 < changed.sum() < len(keys)
+    e, _, _, _ = run(keys, D1, W, eps, 40)
+    _, st_inc, order, _ = run(keys, D2, W, eps, 40, changed=changed, e=e)
+    assert e.counters()["cleared"] > 0
+    _, st_fresh, _, _ = run(keys, D2, W, eps, 40)
+    flags = ESDF_OBS | ESDF_SITE | ESDF_PAR | ESDF_INSIDE
+    np.testing.assert_array_equal(st_inc & flags, st_fresh & flags)
+    np.testing.assert_array_equal((esdf_offsets(st_inc) ** 2).sum(-1),
+                                  (esdf_offsets(st_fresh) ** 2).sum(-1))
+    site = np.abs(D2) <= np.float32(eps)
+    exact = brute_edt2(g, site, W > 0)[order]
+    d2 = (esdf_offsets(st_inc) ** 2).sum(-1)
+    assert np.all(d2 >= exact) and np.mean(d2 == exact) >= 0.9
+    check_parents_are_sites(st_inc, g[order], set(map(tuple, g[site].reshape(-1, 3))))
+
+
+def test_unknown_voxels_stay_unknown():
+    """Voxels with weight 0 are unknown (state 0) and pass nothing on: a
+    fully unknown slab between two observed slabs keeps the far slab's
+    voxels from the near slab's sites."""
+    eps = float(V)
+    obs = lambda c: (c[..., 2] < 0.8) | (c[..., 2] > 1.2)  # noqa: E731
+    keys, D, W, g = tsdf_region((0, 0, 0), (2, 2, 4), lambda c: c[..., 2] - 0.43, observed=obs)
+    _, st, order, _ = run(keys, D, W, eps, 60)
+    unknown = (W == 0)[order]
+    assert unknown.any()
+    assert np.all(st[unknown] == 0)
+    far = (g[order][..., 2] * float(V) > 1.2)
+    assert np.all((st[far] & ESDF_PAR) == 0)  # no site beyond the unknown slab
+
+
+def test_bad_parameters():
+    with pytest.raises(ValueError):
+        oracle.EsdfOracle(float(V), float(V), 1e-4, 256)
+    with pytest.raises(ValueError):
+        oracle.EsdfOracle(float(V), -1.0, 1e-4, 10)
