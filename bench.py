@@ -386,6 +386,24 @@ def main():
             "ms_per_step": ms3, "voxel_updates_per_s": ws * m3.stats()["voxel_updates"] / (ms3 * 1e-3),
             "frames_per_s": ws * n_frames / (ms3 * 1e-3)}
         m3.close()
+        # colour layer (Table I colour fusion): registered colour images
+        colors = torch.from_numpy(synth.configs.room_colors(w).view(np.int32)).cuda()
+        m4 = gt.TsdfMap(w.voxel_size, w.truncation_voxels, w.max_weight, layer=gt.LAYER_COLOR)
+        descs4 = [gt.frame_desc(0, f.sensor, f.T, d, colors[i])
+                  for i, (f, d) in enumerate(zip(w.frames, frames_dev))]
+
+        def s4():
+            m4.reset()
+            for s in range(0, n_frames, args.batch):
+                gt.integrate_batch([m4.handle], descs4[s:s + args.batch])
+        for _ in range(args.warmup):
+            s4()
+        ms4 = timed(s4, args.steps)
+        forms[f"color_batched_{args.batch}"] = {
+            "ms_per_step": ms4, "voxel_updates_per_s": ws * m4.stats()["voxel_updates"] / (ms4 * 1e-3),
+            "frames_per_s": ws * n_frames / (ms4 * 1e-3)}
+        m4.close()
+        del colors
         forms["fp32_batched_speedup_vs_one_frame"] = ms1 / ms
         forms["fp16_batched_speedup_vs_one_frame"] = ms1 / ms2
 

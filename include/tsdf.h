@@ -277,6 +277,70 @@ tsdf_status map_export_color(const tsdf_map* map, int32_t* keys_host, float* rgb
 tsdf_status map_decay_occupancy(tsdf_map* map, float decay_occ, float decay_free,
                                 void* cuda_stream);
 
+/*
+ * map_import — write n blocks into the map from host memory: keys_host
+ * int32 [n][3] block coordinates (each in (-2^20, 2^20), no duplicates),
+ * dist_host and weight_host float32 [n][512] (voxel x + 8 y + 64 z; for an
+ * occupancy map dist is the log-odds and weight_host may be NULL).  Missing
+ * blocks are allocated, present ones overwritten; every written block
+ * counts as changed for the next map_esdf_update.  Values are stored in the
+ * map's storage (FP16 rounds D / tau and W).  Not for colour maps.
+ * Synchronises; uses temporary device memory.
+ */
+tsdf_status map_import(tsdf_map* map, const int32_t* keys_host, const float* dist_host,
+                       const float* weight_host, int64_t n);
+
+/* ESDF parameters: site_eps (m): observed voxels with |D| <= site_eps are
+ * sites; min_weight: voxels with W >= min_weight are observed; max_dist_vox
+ * (1..255): distances are propagated up to this many voxels.  Defaults
+ * (NULL): one voxel, 1e-4, 64. */
+typedef struct {
+  float site_eps;
+  float min_weight;
+  int32_t max_dist_vox;
+} tsdf_esdf_opts;
+
+/*
+ * map_esdf_update — bring the map's ESDF layer (Sec. IV-C) up to date with
+ * the TSDF blocks changed since the previous call (integrated or imported).
+ * Each ESDF voxel is unknown or observed; an observed voxel may be a site and
+ * may hold a parent, the offset to the site it is closest to as found by the
+ * propagation.  Stages, in order: mark sites in the changed blocks (a voxel
+ * that stops being a site, becomes observed or changes sides loses its
+ * parent); clear, in blocks within ceil(max_dist / 8) + 1 blocks of one that
+ * lost a site, every parent that is no longer a site; then repeat until no
+ * block changes: six in-block sweeps (+x, -x, +y, -y, +z, -z) of the update
+ * set, and a face exchange (faces -x, +x, -y, +y, -z, +z) in which the
+ * update set and its face neighbours take, on their faces, a shorter parent
+ * from the adjacent voxel across the face, all reading the states before the
+ * exchange.  A parent is taken only if strictly shorter and within
+ * max_dist.  The first call allocates the layer (8 KiB per pool block) and
+ * fixes the parameters; later calls must pass the same ones.  TSDF maps
+ * only (FP32 or FP16 storage).  Enqueued on cuda_stream; waits for the
+ * stream once per iteration to test for convergence.
+ */
+tsdf_status map_esdf_update(tsdf_map* map, const tsdf_esdf_opts* opts, void* cuda_stream);
+
+/* map_esdf_export — ESDF voxel states of every block, sorted like
+ * map_export: keys_host int32 [n][3], states_host uint32 [n][512] (may be
+ * NULL).  State word: parent offset x, y, z as 9-bit two's complement in
+ * bits 0-8, 9-17, 18-26; bit 27 observed, bit 28 site, bit 29 has a parent,
+ * bit 30 inside (D < 0).  TSDF_ERR_ARG before the first update or for a
+ * wrong n.  Synchronises. */
+tsdf_status map_esdf_export(const tsdf_map* map, int32_t* keys_host, uint32_t* states_host, int64_t n);
+
+/* map_esdf_query — signed Euclidean distance (m) at n points (float32
+ * [n][3], device): the voxel's parent offset length times the voxel size,
+ * negative inside; +-max_dist voxels for an observed voxel without a parent;
+ * NaN for an unknown voxel or a point in no block.  Async on cuda_stream. */
+tsdf_status map_esdf_query(const tsdf_map* map, const float* pts_dev, int64_t n, float* dist_dev,
+                           void* cuda_stream);
+
+/* map_esdf_stats — totals since the layer was allocated or the map reset:
+ * out[0] lowering iterations, out[1] blocks swept, out[2] blocks in face
+ * exchanges, out[3] voxels whose parent was cleared.  Synchronises. */
+tsdf_status map_esdf_stats(const tsdf_map* map, int64_t out[4]);
+
 /* map_reset — drop every block (keeps the allocation), enqueued on
  * cuda_stream; clears the sticky status. */
 tsdf_status map_reset(tsdf_map* map, void* cuda_stream);

@@ -24,6 +24,8 @@ __all__ = ["TsdfError", "Pinhole", "Lidar", "MapOpts", "FrameDesc", "TsdfMap", "
            "MapBuffers", "integrate_depth_static", "STATIC_MAX_BLOCKS", "LAYER_TSDF",
            "LAYER_OCCUPANCY", "LAYER_COLOR", "STORAGE_FP32", "STORAGE_FP16",
            "integrate_color", "query_color", "map_export_color", "map_decay_occupancy",
+           "EsdfOpts", "map_import", "map_esdf_update", "map_esdf_export", "map_esdf_query",
+           "map_esdf_stats",
            "SENSOR_PINHOLE", "SENSOR_LIDAR", "EXPORTED_SYMBOLS"]
 
 STORAGE_FP32, STORAGE_FP16 = 0, 1
@@ -37,7 +39,8 @@ EXPORTED_SYMBOLS = ["map_create", "map_create_ex", "integrate_depth", "integrate
                     "integrate_batch", "query_voxels", "map_sync", "map_num_blocks", "map_stats",
                     "map_export", "map_reset", "map_destroy", "map_timing", "map_kernel_times",
                     "integrate_depth_static", "integrate_color", "query_color",
-                    "map_export_color", "map_decay_occupancy"]
+                    "map_export_color", "map_decay_occupancy", "map_import", "map_esdf_update",
+                    "map_esdf_export", "map_esdf_query", "map_esdf_stats"]
 
 
 class TsdfError(RuntimeError):
@@ -71,6 +74,11 @@ class FrameDesc(ctypes.Structure):
     _fields_ = [("map", ctypes.c_int32), ("kind", ctypes.c_int32), ("pinhole", Pinhole),
                 ("lidar", Lidar), ("depth_dev", ctypes.c_void_p),
                 ("T_world_sensor", ctypes.c_double * 16), ("color_dev", ctypes.c_void_p)]
+
+
+class EsdfOpts(ctypes.Structure):
+    _fields_ = [("site_eps", ctypes.c_float), ("min_weight", ctypes.c_float),
+                ("max_dist_vox", ctypes.c_int32)]
 
 
 class MapBuffers(ctypes.Structure):
@@ -117,6 +125,11 @@ def lib():
                 "query_color": ([P, P, L64, P, P, P], I),
                 "map_export_color": ([P, P, P, P, L64], I),
                 "map_decay_occupancy": ([P, F, F, P], I),
+                "map_import": ([P, P, P, P, L64], I),
+                "map_esdf_update": ([P, ctypes.POINTER(EsdfOpts), P], I),
+                "map_esdf_export": ([P, P, P, L64], I),
+                "map_esdf_query": ([P, P, L64, P, P], I),
+                "map_esdf_stats": ([P, P], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -278,6 +291,44 @@ def map_decay_occupancy(m: int, decay_occ: float, decay_free: float, stream=None
            "map_decay_occupancy")
 
 
+def map_import(m: int, keys, D, W=None):
+    """Write blocks (keys int32 [n,3], D / W float32 [n,512]) into the map."""
+    keys = np.ascontiguousarray(keys, np.int32)
+    D = np.ascontiguousarray(D, np.float32)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None  # noqa: E731
+    W = None if W is None else np.ascontiguousarray(W, np.float32)
+    _check(lib().map_import(m, vp(keys), vp(D), vp(W), len(keys)), "map_import")
+
+
+def map_esdf_update(m: int, site_eps: float | None = None, min_weight: float = 1e-4,
+                    max_dist_vox: int = 64, stream=None):
+    o = None
+    if site_eps is not None:
+        o = ctypes.byref(EsdfOpts(site_eps, min_weight, max_dist_vox))
+    _check(lib().map_esdf_update(m, o, _stream(stream)), "map_esdf_update")
+
+
+def map_esdf_export(m: int):
+    """(keys int32 [n,3] sorted by (x,y,z), states uint32 [n,512])."""
+    n = map_num_blocks(m)
+    keys = np.zeros((n, 3), np.int32)
+    st = np.zeros((n, 512), np.uint32)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(lib().map_esdf_export(m, vp(keys), vp(st), n), "map_esdf_export")
+    return keys, st
+
+
+def map_esdf_query(m: int, pts, dist, stream=None):
+    n = pts.shape[0] if hasattr(pts, "shape") else 0
+    _check(lib().map_esdf_query(m, _dptr(pts), n, _dptr(dist), _stream(stream)), "map_esdf_query")
+
+
+def map_esdf_stats(m: int) -> dict:
+    out = np.zeros(4, np.int64)
+    _check(lib().map_esdf_stats(m, out.ctypes.data_as(ctypes.c_void_p)), "map_esdf_stats")
+    return dict(zip(["iterations", "swept", "pulled", "cleared"], (int(x) for x in out)))
+
+
 def map_reset(m: int, stream=None):
     _check(lib().map_reset(m, _stream(stream)), "map_reset")
 
@@ -343,6 +394,22 @@ class TsdfMap:
 
     def query_color(self, pts, rgb, weight, stream=None):
         query_color(self.handle, pts, rgb, weight, stream)
+
+    def import_blocks(self, keys, D, W=None):
+        map_import(self.handle, keys, D, W)
+
+    def esdf_update(self, site_eps: float | None = None, min_weight: float = 1e-4,
+                    max_dist_vox: int = 64, stream=None):
+        map_esdf_update(self.handle, site_eps, min_weight, max_dist_vox, stream)
+
+    def esdf_export(self):
+        return map_esdf_export(self.handle)
+
+    def esdf_query(self, pts, dist, stream=None):
+        map_esdf_query(self.handle, pts, dist, stream)
+
+    def esdf_stats(self) -> dict:
+        return map_esdf_stats(self.handle)
 
     def decay(self, decay_occ: float, decay_free: float, stream=None):
         map_decay_occupancy(self.handle, decay_occ, decay_free, stream)

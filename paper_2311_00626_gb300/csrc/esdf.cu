@@ -1,0 +1,449 @@
+// ESDF layer kernels (Sec. IV-C) and the map import kernel, sm_103a.
+//
+// The ESDF layer is indexed like the TSDF pool: block p of the pool has the
+// 512 voxel state words st[p * 512 ..].  One update runs the stages of
+// Sec. IV-C in order:
+//
+//   esdf_mark_kernel   mark sites in the blocks changed since the last
+//                      update (the dirty flags the integration sets) and
+//                      reset voxels whose site status, observation or side
+//                      changed; collect the update set and the blocks where
+//                      a site disappeared
+//   esdf_clear_kernel  in every block near one of the latter, drop parents
+//                      that are no longer sites
+//   then, until the update set is empty (the host loops):
+//   esdf_sweep_kernel  six in-block sweeps (+x, -x, +y, -y, +z, -z) of every
+//                      block of the update set, in shared memory
+//   esdf_tlist_kernel  the update set and its existing face neighbours
+//   esdf_pull_kernel   every such block tries, on its faces, the parents of
+//                      the adjacent voxels across the faces, reading the
+//                      states as they were before this step; results go to
+//                      st2
+//   esdf_apply_kernel  copy back the blocks that changed; they form the next
+//                      update set
+//
+// All distance arithmetic is on integer offsets (squared lengths), so the
+// result is exact and does not depend on the order in which CTAs run.
+#include <cmath>
+
+#include "tsdf_internal.cuh"
+
+namespace gbt {
+namespace {
+
+constexpr int kEsdfThreads = 128;  // 4 voxels per thread
+
+__device__ __forceinline__ int off_comp(uint32_t s, int axis) {
+  const int raw = (int)((s >> (9 * axis)) & 511u);
+  return raw >= 256 ? raw - 512 : raw;
+}
+
+__device__ __forceinline__ int dist2(uint32_t s) {
+  const int x = off_comp(s, 0), y = off_comp(s, 1), z = off_comp(s, 2);
+  return x * x + y * y + z * z;
+}
+
+// Voxel p tries the parent of its neighbour q, which lies at p + (dx, dy, dz):
+// taken if p is observed and not a site, q has a parent, and the offset from
+// p to that parent is within max_dist and strictly shorter than p's own.
+__device__ __forceinline__ bool relax(uint32_t& p, uint32_t q, int dx, int dy, int dz, int max2) {
+  if (!(p & kEsdfObs) || (p & kEsdfSite) || !(q & kEsdfPar)) return false;
+  const int cx = off_comp(q, 0) + dx, cy = off_comp(q, 1) + dy, cz = off_comp(q, 2) + dz;
+  const int c2 = cx * cx + cy * cy + cz * cz;
+  if (c2 > max2) return false;
+  if ((p & kEsdfPar) && c2 >= dist2(p)) return false;
+  p = (p & ~kEsdfOffMask) | kEsdfPar | ((uint32_t)cx & 511u) | (((uint32_t)cy & 511u) << 9) |
+      (((uint32_t)cz & 511u) << 18);
+  return true;
+}
+
+__device__ __forceinline__ uint32_t n_blocks(const MapDev& m) {
+  return (uint32_t)min((unsigned long long)m.max_blocks, __ldcg(m.counters + kCntBlocks));
+}
+
+// Pool index of the block with coordinates (x, y, z), or -1.
+__device__ __forceinline__ int pool_of(const MapDev& m, int x, int y, int z) {
+  const int slot = hash_find(m, pack_key(x, y, z));
+  if (slot < 0) return -1;
+  const int val = m.vals[slot];
+  return val >= 0 ? val : -1;
+}
+
+// Append block p to an update set (list, size) unless this generation has it already.
+__device__ __forceinline__ void add_update(const EsdfDev& e, uint32_t* list, uint32_t* size,
+                                           uint32_t p, uint32_t gen) {
+  if (atomicExch(e.stamp_s + p, gen) != gen) list[atomicAdd(size, 1u)] = p;
+}
+
+// TSDF value of voxel l of pool block p (FP32 storage {D, W}; FP16 {D/tau, W}).
+__device__ __forceinline__ void tsdf_at(const MapDev& m, uint32_t p, int l, float& D, float& W) {
+  if (m.storage == kStorageF16) {
+    const __half2 h = reinterpret_cast<const __half2*>(m.pool)[(size_t)p * 512 + l];
+    D = __low2float(h) * m.tau;
+    W = __high2float(h);
+  } else {
+    const float2 v = reinterpret_cast<const float2*>(m.pool)[(size_t)p * 512 + l];
+    D = v.x;
+    W = v.y;
+  }
+}
+
+// ------------------------------------------------------------- mark sites
+
+__global__ void __launch_bounds__(kEsdfThreads)
+    esdf_mark_kernel(const MapDev m, const EsdfDev e, uint32_t gen) {
+  const uint32_t nb = n_blocks(m);
+  const int t = threadIdx.x;
+  for (uint32_t p = blockIdx.x; p < nb; p += gridDim.x) {
+    if (!m.dirty[p]) continue;  // same value for every thread of the CTA
+    bool any = false, lost = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int l = 4 * t + i;
+      float D, W;
+      tsdf_at(m, p, l, D, W);
+      const bool obs = W >= e.min_weight;
+      const bool site = obs && fabsf(D) <= e.site_eps;
+      const bool inside = obs && D < 0.0f;
+      uint32_t* sp = e.st + (size_t)p * 512 + l;
+      const uint32_t old = *sp;
+      uint32_t s = old;
+      if (site) {
+        s = kEsdfObs | kEsdfSite | kEsdfPar | (inside ? kEsdfInside : 0u);
+      } else if (old & kEsdfSite) {
+        s = obs ? (kEsdfObs | (inside ? kEsdfInside : 0u)) : 0u;
+        lost = true;
+      } else if (!obs) {
+        s = 0u;
+      } else if (!(old & kEsdfObs) || ((old & kEsdfInside) != 0u) != inside) {
+        s = kEsdfObs | (inside ? kEsdfInside : 0u);
+      }
+      if (s != old) {
+        *sp = s;
+        any = true;
+      }
+    }
+    any = __syncthreads_or(any);   // also: every thread has read dirty[p]
+    lost = __syncthreads_or(lost);
+    if (t == 0) {
+      m.dirty[p] = 0;
+      if (any) add_update(e, e.list[0], e.cnt, p, gen);
+      if (lost) e.clist[atomicAdd(e.cnt + 3, 1u)] = p;
+    }
+  }
+}
+
+// ---------------------------------------------------------- clear invalid
+
+constexpr int kClearChunk = 512;
+
+__global__ void __launch_bounds__(kEsdfThreads)
+    esdf_clear_kernel(const MapDev m, const EsdfDev e, uint32_t gen) {
+  __shared__ int s_c[kClearChunk][3];
+  const uint32_t nc = __ldcg(e.cnt + 3);
+  if (nc == 0) return;
+  const uint32_t nb = n_blocks(m);
+  const int t = threadIdx.x;
+  const int R = (e.max_dist + 7) / 8 + 1;
+  unsigned long long my_cleared = 0;
+  for (uint32_t p = blockIdx.x; p < nb; p += gridDim.x) {
+    const unsigned long long key = m.block_keys[p];
+    const int bx = key_coord(key, 0), by = key_coord(key, 1), bz = key_coord(key, 2);
+    bool near = false;
+    for (uint32_t c0 = 0; c0 < nc; c0 += kClearChunk) {
+      const uint32_t cn = min((uint32_t)kClearChunk, nc - c0);
+      __syncthreads();
+      for (uint32_t i = t; i < cn; i += kEsdfThreads) {
+        const unsigned long long ck = m.block_keys[e.clist[c0 + i]];
+        s_c[i][0] = key_coord(ck, 0);
+        s_c[i][1] = key_coord(ck, 1);
+        s_c[i][2] = key_coord(ck, 2);
+      }
+      __syncthreads();
+      for (uint32_t i = t; i < cn && !near; i += kEsdfThreads)
+        near = abs(bx - s_c[i][0]) <= R && abs(by - s_c[i][1]) <= R && abs(bz - s_c[i][2]) <= R;
+      if (__syncthreads_or(near)) {
+        near = true;
+        break;
+      }
+    }
+    if (!near) continue;  // uniform: set by __syncthreads_or
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int l = 4 * t + i;
+      uint32_t* sp = e.st + (size_t)p * 512 + l;
+      const uint32_t s = *sp;
+      if (!(s & kEsdfPar) || (s & kEsdfSite)) continue;
+      // parent voxel in global voxel coordinates, then its block and index
+      const int gx = 8 * bx + (l & 7) + off_comp(s, 0);
+      const int gy = 8 * by + ((l >> 3) & 7) + off_comp(s, 1);
+      const int gz = 8 * bz + (l >> 6) + off_comp(s, 2);
+      const int pbx = gx >> 3, pby = gy >> 3, pbz = gz >> 3;
+      const int pp = (pbx == bx && pby == by && pbz == bz) ? (int)p : pool_of(m, pbx, pby, pbz);
+      const bool ok = pp >= 0 &&
+                      (e.st[(size_t)pp * 512 + (gx & 7) + 8 * (gy & 7) + 64 * (gz & 7)] & kEsdfSite);
+      if (!ok) {
+        *sp = s & ~(kEsdfPar | kEsdfOffMask);
+        ++my_cleared;
+        any = true;
+      }
+    }
+    if (__syncthreads_or(any) && t == 0) add_update(e, e.list[0], e.cnt, p, gen);
+  }
+  if (my_cleared) atomicAdd(e.cleared, my_cleared);
+}
+
+// ------------------------------------------------------------ lower ESDF
+
+// Six in-block sweeps of every block of the current update set.  64 threads
+// sweep the 64 lines of an axis direction, one line each.
+__global__ void __launch_bounds__(64)
+    esdf_sweep_kernel(const EsdfDev e, const uint32_t* __restrict__ list, const uint32_t* size) {
+  __shared__ uint32_t s[512];
+  const uint32_t n = __ldcg(size);
+  const int t = threadIdx.x;
+  const int max2 = e.max_dist * e.max_dist;
+  for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
+    const uint32_t p = list[k];
+    uint32_t* g = e.st + (size_t)p * 512;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s[t + 64 * i] = g[t + 64 * i];
+    __syncthreads();
+    const int a = t & 7, c = t >> 3;  // coordinates on the two other axes, in axis order
+#pragma unroll
+    for (int axis = 0; axis < 3; ++axis) {
+      // linear index of position i along `axis` on this thread's line
+      const int stride = axis == 0 ? 1 : (axis == 1 ? 8 : 64);
+      const int base = axis == 0 ? 8 * a + 64 * c : (axis == 1 ? a + 64 * c : a + 8 * c);
+#pragma unroll
+      for (int dir = 0; dir < 2; ++dir) {
+        const int step = dir == 0 ? -1 : 1;  // position of the previous voxel relative to i
+#pragma unroll
+        for (int k2 = 1; k2 < 8; ++k2) {
+          const int i = dir == 0 ? k2 : 7 - k2;
+          const int j = i + step;
+          relax(s[base + stride * i], s[base + stride * j], axis == 0 ? step : 0,
+                axis == 1 ? step : 0, axis == 2 ? step : 0, max2);
+        }
+        __syncthreads();
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) g[t + 64 * i] = s[t + 64 * i];
+  }
+}
+
+// tlist = the current update set and its existing face neighbours.
+__global__ void esdf_tlist_kernel(const MapDev m, const EsdfDev e, const uint32_t* __restrict__ list,
+                                  const uint32_t* size, uint32_t gen_t) {
+  const uint32_t n = __ldcg(size);
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const uint32_t p = list[k];
+    const unsigned long long key = m.block_keys[p];
+    const int bx = key_coord(key, 0), by = key_coord(key, 1), bz = key_coord(key, 2);
+    if (atomicExch(e.stamp_t + p, gen_t) != gen_t) e.tlist[atomicAdd(e.cnt + 2, 1u)] = p;
+    for (int f = 0; f < 6; ++f) {
+      const int d = (f & 1) ? 1 : -1;
+      const int q = pool_of(m, bx + (f >> 1 == 0 ? d : 0), by + (f >> 1 == 1 ? d : 0),
+                            bz + (f >> 1 == 2 ? d : 0));
+      if (q >= 0 && atomicExch(e.stamp_t + q, gen_t) != gen_t)
+        e.tlist[atomicAdd(e.cnt + 2, 1u)] = (uint32_t)q;
+    }
+  }
+}
+
+// Face exchange: each voxel on a face of the block tries the parent of the
+// voxel across that face in the neighbouring block, faces in -x, +x, -y,
+// +y, -z, +z order; reads st only, writes the block to st2 if it changed.
+__global__ void __launch_bounds__(kEsdfThreads) esdf_pull_kernel(const MapDev m, const EsdfDev e) {
+  __shared__ int s_nb[6];
+  const uint32_t n = __ldcg(e.cnt + 2);
+  const int t = threadIdx.x;
+  const int max2 = e.max_dist * e.max_dist;
+  for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
+    const uint32_t p = e.tlist[k];
+    __syncthreads();
+    if (t < 6) {
+      const unsigned long long key = m.block_keys[p];
+      const int d = (t & 1) ? 1 : -1;
+      s_nb[t] = pool_of(m, key_coord(key, 0) + (t >> 1 == 0 ? d : 0),
+                        key_coord(key, 1) + (t >> 1 == 1 ? d : 0),
+                        key_coord(key, 2) + (t >> 1 == 2 ? d : 0));
+    }
+    __syncthreads();
+    uint32_t v[4];
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int l = 4 * t + i;
+      const int x = l & 7, y = (l >> 3) & 7, z = l >> 6;
+      const int c[3] = {x, y, z};
+      v[i] = e.st[(size_t)p * 512 + l];
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        const int axis = f >> 1;
+        const int mine = (f & 1) ? 7 : 0;
+        if (c[axis] != mine || s_nb[f] < 0) continue;
+        const int ql = l + (axis == 0 ? 1 : (axis == 1 ? 8 : 64)) * (7 - 2 * mine);
+        const uint32_t q = e.st[(size_t)s_nb[f] * 512 + ql];
+        const int d = (f & 1) ? 1 : -1;
+        any |= relax(v[i], q, axis == 0 ? d : 0, axis == 1 ? d : 0, axis == 2 ? d : 0, max2);
+      }
+    }
+    any = __syncthreads_or(any);
+    if (any) {
+      uint4* dst = reinterpret_cast<uint4*>(e.st2 + (size_t)p * 512) + t;
+      *dst = make_uint4(v[0], v[1], v[2], v[3]);
+    }
+    if (t == 0) e.tchanged[k] = any ? 1 : 0;
+  }
+}
+
+// Copy the changed blocks back; they form the next update set.
+__global__ void __launch_bounds__(kEsdfThreads)
+    esdf_apply_kernel(const EsdfDev e, uint32_t* next, uint32_t* next_size, uint32_t gen_next) {
+  const uint32_t n = __ldcg(e.cnt + 2);
+  const int t = threadIdx.x;
+  for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
+    if (!e.tchanged[k]) continue;
+    const uint32_t p = e.tlist[k];
+    reinterpret_cast<uint4*>(e.st + (size_t)p * 512)[t] =
+        reinterpret_cast<const uint4*>(e.st2 + (size_t)p * 512)[t];
+    if (t == 0) add_update(e, next, next_size, p, gen_next);
+  }
+}
+
+// ---------------------------------------------------------------- query
+
+// Signed distance (m) at each point: the parent offset's length times the
+// voxel size, negative inside; max_dist for an observed voxel without a
+// parent; NaN for an unknown voxel or a point outside every block.
+__global__ void esdf_query_kernel(const MapDev m, const EsdfDev e, const float* __restrict__ pts,
+                                  int64_t n, float* __restrict__ dist) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float out = __int_as_float(0x7fc00000);
+  const float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+  const float gx = floorf(__fdiv_rn(x, m.v)), gy = floorf(__fdiv_rn(y, m.v)), gz = floorf(__fdiv_rn(z, m.v));
+  const float lim = 8.0f * 1048576.0f;
+  if (fabsf(gx) < lim && fabsf(gy) < lim && fabsf(gz) < lim) {
+    const int ix = (int)gx, iy = (int)gy, iz = (int)gz;
+    const int p = pool_of(m, ix >> 3, iy >> 3, iz >> 3);
+    if (p >= 0) {
+      const uint32_t s = e.st[(size_t)p * 512 + (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7)];
+      if (s & kEsdfObs) {
+        const float d = (s & kEsdfPar) ? sqrtf((float)dist2(s)) : (float)e.max_dist;
+        out = ((s & kEsdfInside) ? -d : d) * m.v;
+      }
+    }
+  }
+  dist[i] = out;
+}
+
+// ---------------------------------------------------------------- import
+
+// One CTA per input block: find or insert its key (a new key takes the next
+// pool block), write its voxels in the map's storage, mark it changed.
+__global__ void __launch_bounds__(kEsdfThreads)
+    import_kernel(const MapDev m, const int32_t* __restrict__ keys, const float* __restrict__ D,
+                  const float* __restrict__ W, int64_t n) {
+  __shared__ int s_pool;
+  const int t = threadIdx.x;
+  for (int64_t b = blockIdx.x; b < n; b += gridDim.x) {
+    __syncthreads();
+    if (t == 0) {
+      const unsigned long long key = pack_key(keys[3 * b], keys[3 * b + 1], keys[3 * b + 2]);
+      int pool = -1;
+      uint32_t slot = hash_key(key) & m.cap_mask;
+      for (uint32_t probe = 0; probe <= m.cap_mask; ++probe) {
+        const unsigned long long old = atomicCAS(m.keys + slot, kEmptyKey, key);
+        if (old == kEmptyKey) {
+          const unsigned long long q = atomicAdd(m.counters + kCntBlocks, 1ull);
+          if (q < (unsigned long long)m.max_blocks) {
+            m.block_keys[q] = key;
+            m.vals[slot] = (int)q;
+            pool = (int)q;
+          } else {
+            m.vals[slot] = -1;
+            atomicOr(m.counters + kCntStatus, (unsigned long long)kStPoolFull);
+          }
+          break;
+        }
+        if (old == key) {
+          pool = m.vals[slot];
+          break;
+        }
+        slot = (slot + 1) & m.cap_mask;
+        if (probe == m.cap_mask) atomicOr(m.counters + kCntStatus, (unsigned long long)kStHashFull);
+      }
+      s_pool = pool;
+    }
+    __syncthreads();
+    const int pool = s_pool;
+    if (pool < 0) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int l = 4 * t + i;
+      const float d = D[b * 512 + l], w = W[b * 512 + l];
+      if (m.storage == kStorageOcc) {
+        reinterpret_cast<float*>(m.pool)[(size_t)pool * 512 + l] = d;
+      } else if (m.storage == kStorageF16) {
+        reinterpret_cast<__half2*>(m.pool)[(size_t)pool * 512 + l] = __floats2half2_rn(d * m.inv_tau, w);
+      } else {
+        reinterpret_cast<float2*>(m.pool)[(size_t)pool * 512 + l] = make_float2(d, w);
+      }
+    }
+    if (t == 0 && m.dirty) m.dirty[pool] = 1;
+  }
+}
+
+int grid_for(int per_sm) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, sms) * per_sm;
+}
+
+}  // namespace
+
+cudaError_t launch_esdf_mark(const MapDev& m, const EsdfDev& e, uint32_t gen, cudaStream_t s) {
+  esdf_mark_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(m, e, gen);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_esdf_clear(const MapDev& m, const EsdfDev& e, uint32_t gen, cudaStream_t s) {
+  esdf_clear_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(m, e, gen);
+  return cudaGetLastError();
+}
+
+// One lowering iteration: sweep the current set, build tlist, exchange
+// faces, apply.  The caller zeroes the tlist and next-set sizes first.
+cudaError_t launch_esdf_iteration(const MapDev& m, const EsdfDev& e, int cur, uint32_t gen_t,
+                                  uint32_t gen_next, cudaStream_t s) {
+  uint32_t* list = cur ? e.list[1] : e.list[0];
+  uint32_t* next = cur ? e.list[0] : e.list[1];
+  esdf_sweep_kernel<<<grid_for(16), 64, 0, s>>>(e, list, e.cnt + cur);
+  esdf_tlist_kernel<<<grid_for(2), 256, 0, s>>>(m, e, list, e.cnt + cur, gen_t);
+  esdf_pull_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(m, e);
+  esdf_apply_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(e, next, e.cnt + (1 - cur), gen_next);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_esdf_query(const MapDev& m, const EsdfDev& e, const float* pts, int64_t n,
+                              float* dist, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int threads = 256;
+  esdf_query_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(m, e, pts, n, dist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_import(const MapDev& m, const int32_t* keys, const float* D, const float* W,
+                          int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  import_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(m, keys, D, W, n);
+  return cudaGetLastError();
+}
+
+}  // namespace gbt

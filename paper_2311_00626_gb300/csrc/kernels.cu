@@ -50,17 +50,6 @@ __device__ __forceinline__ int hash_insert(const MapDev& m, unsigned long long k
   return -1;
 }
 
-__device__ __forceinline__ int hash_find(const MapDev& m, unsigned long long key) {
-  uint32_t slot = hash_key(key) & m.cap_mask;
-  for (uint32_t probe = 0; probe <= m.cap_mask; ++probe) {
-    const unsigned long long k = m.keys[slot];
-    if (k == key) return (int)slot;
-    if (k == kEmptyKey) return -1;
-    slot = (slot + 1) & m.cap_mask;
-  }
-  return -1;
-}
-
 // ------------------------------------------------- block-grid traversal
 
 __device__ __forceinline__ void claim_block(const MapDev& m, unsigned long long key, int bit) {
@@ -727,6 +716,7 @@ __global__ void __launch_bounds__(kIntegrateThreads)
     if (t == 0) {
       m.mask[slot] = 0u;
       if (fresh) m.vals[slot] = pool;
+      if (m.dirty && val != -1) m.dirty[pool] = 1;
     }
   }
   __syncthreads();

@@ -5,6 +5,7 @@
 // once to FP32) and enqueues two kernels: the band allocator and the
 // per-voxel integrator (Sec. IV-B).  Nothing here touches voxel data.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -15,6 +16,7 @@
 #include "tsdf_internal.cuh"
 
 using gbt::BatchParams;
+using gbt::EsdfDev;
 using gbt::FrameDev;
 using gbt::MapDev;
 
@@ -49,6 +51,13 @@ struct tsdf_map {
   bool timing;
   std::vector<cudaEvent_t> events;
   size_t n_timed;
+  // ESDF layer, allocated by the first map_esdf_update
+  bool esdf_on;
+  EsdfDev esdf;
+  tsdf_esdf_opts esdf_opts;
+  uint32_t esdf_gen;      // generation of the last update set / tlist built
+  uint32_t* esdf_host;    // pinned copy of esdf.cnt
+  int64_t esdf_iters, esdf_swept, esdf_pulled;
 };
 
 namespace {
@@ -272,6 +281,21 @@ void free_map(tsdf_map* m) {
   cudaFree(m->mask1);
   cudaFree(m->list1);
   cudaFree(m->ctl1);
+  cudaFree(m->dev.dirty);
+  if (m->esdf_on) {
+    cudaFree(m->esdf.st);
+    cudaFree(m->esdf.st2);
+    cudaFree(m->esdf.list[0]);
+    cudaFree(m->esdf.list[1]);
+    cudaFree(m->esdf.tlist);
+    cudaFree(m->esdf.clist);
+    cudaFree(m->esdf.stamp_s);
+    cudaFree(m->esdf.stamp_t);
+    cudaFree(m->esdf.tchanged);
+    cudaFree(m->esdf.cnt);
+    cudaFree(m->esdf.cleared);
+    cudaFreeHost(m->esdf_host);
+  }
   if (m->aux) cudaStreamDestroy(m->aux);
   for (int i = 0; i < 4; ++i) {
     if (m->ev_alloc[i]) cudaEventDestroy(m->ev_alloc[i]);
@@ -382,6 +406,7 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
             cudaMalloc(&m->mask1, sizeof(uint32_t) * cap) == cudaSuccess &&
             cudaMalloc(&m->list1, sizeof(uint32_t) * o.max_blocks) == cudaSuccess &&
             cudaMalloc(&m->ctl1, sizeof(unsigned int) * 4) == cudaSuccess &&
+            cudaMalloc(&d.dirty, (size_t)o.max_blocks) == cudaSuccess &&
             cudaStreamCreateWithFlags(&m->aux, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&m->ev_start, cudaEventDisableTiming) == cudaSuccess;
   for (int i = 0; ok && i < 4; ++i)
@@ -391,6 +416,7 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
     ok = gbt::launch_reset(d, m->cap, 0) == cudaSuccess &&
          cudaMemsetAsync(m->mask1, 0, sizeof(uint32_t) * cap, 0) == cudaSuccess &&
          cudaMemsetAsync(m->ctl1, 0, sizeof(unsigned int) * 4, 0) == cudaSuccess &&
+         cudaMemsetAsync(d.dirty, 0, (size_t)o.max_blocks, 0) == cudaSuccess &&
          cudaDeviceSynchronize() == cudaSuccess;
   if (!ok) {
     free_map(m);
@@ -680,14 +706,216 @@ tsdf_status map_decay_occupancy(tsdf_map* map, float decay_occ, float decay_free
   return TSDF_OK;
 }
 
+// ------------------------------------------------------------------ ESDF
+
+namespace {
+
+bool esdf_layer_ok(const tsdf_map* m) {
+  return m->storage == TSDF_STORAGE_FP32 || m->storage == TSDF_STORAGE_FP16;
+}
+
+tsdf_status esdf_alloc(tsdf_map* m, const tsdf_esdf_opts& o) {
+  EsdfDev& e = m->esdf;
+  std::memset(&e, 0, sizeof(e));
+  const size_t nb = (size_t)m->max_blocks;
+  bool ok = cudaMalloc(&e.st, sizeof(uint32_t) * 512 * nb) == cudaSuccess &&
+            cudaMalloc(&e.st2, sizeof(uint32_t) * 512 * nb) == cudaSuccess &&
+            cudaMalloc(&e.list[0], sizeof(uint32_t) * nb) == cudaSuccess &&
+            cudaMalloc(&e.list[1], sizeof(uint32_t) * nb) == cudaSuccess &&
+            cudaMalloc(&e.tlist, sizeof(uint32_t) * nb) == cudaSuccess &&
+            cudaMalloc(&e.clist, sizeof(uint32_t) * nb) == cudaSuccess &&
+            cudaMalloc(&e.stamp_s, sizeof(uint32_t) * nb) == cudaSuccess &&
+            cudaMalloc(&e.stamp_t, sizeof(uint32_t) * nb) == cudaSuccess &&
+            cudaMalloc(&e.tchanged, nb) == cudaSuccess &&
+            cudaMalloc(&e.cnt, sizeof(uint32_t) * 4) == cudaSuccess &&
+            cudaMalloc(&e.cleared, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMallocHost(&m->esdf_host, sizeof(uint32_t) * 4) == cudaSuccess;
+  if (ok)
+    ok = cudaMemset(e.st, 0, sizeof(uint32_t) * 512 * nb) == cudaSuccess &&
+         cudaMemset(e.stamp_s, 0, sizeof(uint32_t) * nb) == cudaSuccess &&
+         cudaMemset(e.stamp_t, 0, sizeof(uint32_t) * nb) == cudaSuccess &&
+         cudaMemset(e.cnt, 0, sizeof(uint32_t) * 4) == cudaSuccess &&
+         cudaMemset(e.cleared, 0, sizeof(unsigned long long)) == cudaSuccess &&
+         cudaDeviceSynchronize() == cudaSuccess;
+  m->esdf_on = true;  // free_map releases whatever was allocated
+  if (!ok) return cuda_fail();
+  e.site_eps = o.site_eps;
+  e.min_weight = o.min_weight;
+  e.max_dist = o.max_dist_vox;
+  m->esdf_opts = o;
+  m->esdf_gen = 0;
+  m->esdf_iters = m->esdf_swept = m->esdf_pulled = 0;
+  return TSDF_OK;
+}
+
+tsdf_status esdf_read_counts(tsdf_map* m, cudaStream_t s) {
+  if (cudaMemcpyAsync(m->esdf_host, m->esdf.cnt, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return cuda_fail();
+  return TSDF_OK;
+}
+
+}  // namespace
+
+tsdf_status map_esdf_update(tsdf_map* map, const tsdf_esdf_opts* opts, void* cuda_stream) {
+  if (!map || !esdf_layer_ok(map)) return TSDF_ERR_ARG;
+  if (!on_device(map)) return TSDF_ERR_STATE;
+  tsdf_esdf_opts o{map->v, 1e-4f, 64};
+  if (opts) o = *opts;
+  if (!(o.site_eps >= 0.0f) || !std::isfinite(o.site_eps) || !std::isfinite(o.min_weight) ||
+      o.max_dist_vox < 1 || o.max_dist_vox > 255)
+    return TSDF_ERR_ARG;
+  if (map->esdf_on && (o.site_eps != map->esdf_opts.site_eps ||
+                       o.min_weight != map->esdf_opts.min_weight ||
+                       o.max_dist_vox != map->esdf_opts.max_dist_vox))
+    return TSDF_ERR_ARG;  // parameters are fixed by the first update
+  if (!map->esdf_on) {
+    tsdf_status st = esdf_alloc(map, o);
+    if (st != TSDF_OK) return st;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  EsdfDev& e = map->esdf;
+  // mark sites and clear invalid parents: update set 0 gets generation g
+  const uint32_t g = ++map->esdf_gen;
+  if (cudaMemsetAsync(e.cnt, 0, sizeof(uint32_t) * 4, s) != cudaSuccess ||
+      gbt::launch_esdf_mark(map->dev, e, g, s) != cudaSuccess ||
+      gbt::launch_esdf_clear(map->dev, e, g, s) != cudaSuccess)
+    return cuda_fail();
+  tsdf_status st = esdf_read_counts(map, s);
+  if (st != TSDF_OK) return st;
+  // lower until no block changes
+  int cur = 0;
+  uint32_t n = map->esdf_host[0];
+  while (n > 0) {
+    map->esdf_iters += 1;
+    map->esdf_swept += n;
+    const uint32_t gen_t = ++map->esdf_gen, gen_next = ++map->esdf_gen;
+    if (cudaMemsetAsync(e.cnt + 2, 0, sizeof(uint32_t), s) != cudaSuccess ||
+        cudaMemsetAsync(e.cnt + (1 - cur), 0, sizeof(uint32_t), s) != cudaSuccess ||
+        gbt::launch_esdf_iteration(map->dev, e, cur, gen_t, gen_next, s) != cudaSuccess)
+      return cuda_fail();
+    st = esdf_read_counts(map, s);
+    if (st != TSDF_OK) return st;
+    map->esdf_pulled += map->esdf_host[2];
+    cur = 1 - cur;
+    n = map->esdf_host[cur];
+  }
+  // the next update starts from set 0
+  if (cur == 1 && cudaMemsetAsync(e.cnt + 1, 0, sizeof(uint32_t), s) != cudaSuccess) return cuda_fail();
+  return TSDF_OK;
+}
+
+tsdf_status map_esdf_stats(const tsdf_map* map, int64_t out[4]) {
+  if (!map || !out) return TSDF_ERR_ARG;
+  unsigned long long cleared = 0;
+  if (map->esdf_on && (cudaDeviceSynchronize() != cudaSuccess ||
+                       cudaMemcpy(&cleared, map->esdf.cleared, sizeof(cleared), cudaMemcpyDeviceToHost) !=
+                           cudaSuccess))
+    return cuda_fail();
+  out[0] = map->esdf_iters;
+  out[1] = map->esdf_swept;
+  out[2] = map->esdf_pulled;
+  out[3] = (int64_t)cleared;
+  return TSDF_OK;
+}
+
+tsdf_status map_esdf_export(const tsdf_map* map, int32_t* keys_host, uint32_t* states_host, int64_t n) {
+  if (!map || !keys_host || !map->esdf_on) return TSDF_ERR_ARG;
+  int64_t nb = 0;
+  tsdf_status st = map_num_blocks(map, &nb);
+  if (st != TSDF_OK) return st;
+  if (n != nb) return TSDF_ERR_ARG;
+  if (nb == 0) return TSDF_OK;
+  std::vector<unsigned long long> bk(nb);
+  std::vector<uint32_t> all;
+  if (cudaMemcpy(bk.data(), map->dev.block_keys, sizeof(unsigned long long) * nb,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_fail();
+  if (states_host) {
+    all.resize((size_t)nb * 512);
+    if (cudaMemcpy(all.data(), map->esdf.st, sizeof(uint32_t) * all.size(), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return cuda_fail();
+  }
+  std::vector<int64_t> order(nb);
+  std::iota(order.begin(), order.end(), 0);
+  auto coords = [&](int64_t i, int axis) { return gbt::key_coord(bk[i], axis); };
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    for (int ax = 0; ax < 3; ++ax)
+      if (coords(a, ax) != coords(b, ax)) return coords(a, ax) < coords(b, ax);
+    return false;
+  });
+  for (int64_t r = 0; r < nb; ++r) {
+    const int64_t i = order[r];
+    for (int ax = 0; ax < 3; ++ax) keys_host[3 * r + ax] = coords(i, ax);
+    if (states_host) std::memcpy(states_host + 512 * r, all.data() + 512 * i, sizeof(uint32_t) * 512);
+  }
+  return TSDF_OK;
+}
+
+tsdf_status map_esdf_query(const tsdf_map* map, const float* pts_dev, int64_t n, float* dist_dev,
+                           void* cuda_stream) {
+  if (!map || !map->esdf_on || n < 0 || (n > 0 && (!pts_dev || !dist_dev))) return TSDF_ERR_ARG;
+  if (!on_device(map)) return TSDF_ERR_STATE;
+  if (gbt::launch_esdf_query(map->dev, map->esdf, pts_dev, n, dist_dev, (cudaStream_t)cuda_stream) !=
+      cudaSuccess)
+    return cuda_fail();
+  return TSDF_OK;
+}
+
+tsdf_status map_import(tsdf_map* map, const int32_t* keys_host, const float* dist_host,
+                       const float* weight_host, int64_t n) {
+  if (!map || n < 0 || (n > 0 && (!keys_host || !dist_host))) return TSDF_ERR_ARG;
+  if (map->storage == gbt::kStorageColor) return TSDF_ERR_ARG;
+  if (n > 0 && map->storage != gbt::kStorageOcc && !weight_host) return TSDF_ERR_ARG;
+  if (!on_device(map)) return TSDF_ERR_STATE;
+  if (n == 0) return TSDF_OK;
+  std::vector<std::array<int32_t, 3>> ks((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int a = 0; a < 3; ++a) {
+      const int32_t c = keys_host[3 * i + a];
+      if (c <= -gbt::kKeyBias || c >= gbt::kKeyBias) return TSDF_ERR_ARG;
+      ks[i][a] = c;
+    }
+  }
+  std::sort(ks.begin(), ks.end());
+  if (std::adjacent_find(ks.begin(), ks.end()) != ks.end()) return TSDF_ERR_ARG;  // duplicate keys
+  int32_t* dk = nullptr;
+  float *dD = nullptr, *dW = nullptr;
+  const size_t vox = (size_t)n * 512;
+  std::vector<float> zeros;
+  if (!weight_host) zeros.assign(vox, 0.0f);
+  bool ok = cudaMalloc(&dk, sizeof(int32_t) * 3 * n) == cudaSuccess &&
+            cudaMalloc(&dD, sizeof(float) * vox) == cudaSuccess &&
+            cudaMalloc(&dW, sizeof(float) * vox) == cudaSuccess &&
+            cudaMemcpy(dk, keys_host, sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(dD, dist_host, sizeof(float) * vox, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(dW, weight_host ? weight_host : zeros.data(), sizeof(float) * vox,
+                       cudaMemcpyHostToDevice) == cudaSuccess &&
+            gbt::launch_import(map->dev, dk, dD, dW, n, 0) == cudaSuccess &&
+            cudaDeviceSynchronize() == cudaSuccess;
+  cudaFree(dk);
+  cudaFree(dD);
+  cudaFree(dW);
+  if (!ok) return cuda_fail();
+  return TSDF_OK;
+}
+
 tsdf_status map_reset(tsdf_map* map, void* cuda_stream) {
   if (!map) return TSDF_ERR_ARG;
   if (!on_device(map)) return TSDF_ERR_STATE;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (gbt::launch_reset(map->dev, map->cap, s) != cudaSuccess ||
       cudaMemsetAsync(map->mask1, 0, sizeof(uint32_t) * map->cap, s) != cudaSuccess ||
-      cudaMemsetAsync(map->ctl1, 0, sizeof(unsigned int) * 4, s) != cudaSuccess)
+      cudaMemsetAsync(map->ctl1, 0, sizeof(unsigned int) * 4, s) != cudaSuccess ||
+      cudaMemsetAsync(map->dev.dirty, 0, (size_t)map->max_blocks, s) != cudaSuccess)
     return cuda_fail();
+  if (map->esdf_on &&
+      (cudaMemsetAsync(map->esdf.st, 0, sizeof(uint32_t) * 512 * map->max_blocks, s) != cudaSuccess ||
+       cudaMemsetAsync(map->esdf.cleared, 0, sizeof(unsigned long long), s) != cudaSuccess))
+    return cuda_fail();
+  map->esdf_iters = map->esdf_swept = map->esdf_pulled = 0;
   map->status_seen = 0;
   map->frames = 0;
   return TSDF_OK;

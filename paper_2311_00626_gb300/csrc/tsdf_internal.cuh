@@ -74,6 +74,29 @@ struct MapDev {
   float l_occ, l_free;            // occupancy layer: log-odds added per update
   int32_t weighting;              // TSDF weight: bit 0 inverse square depth, bit 1 drop-off
   float dropoff;                  // drop-off start behind the surface (m)
+  uint8_t* dirty;                 // [max_blocks] 1 = changed since the last ESDF update
+                                  // (may be null: no tracking)
+};
+
+// ESDF layer of a map (Sec. IV-C), indexed like the pool.  State word per
+// voxel: parent offset x, y, z as 9-bit two's complement in bits 0-8, 9-17,
+// 18-26; kEsdfObs, kEsdfSite, kEsdfPar (has a parent), kEsdfInside.
+constexpr uint32_t kEsdfObs = 1u << 27, kEsdfSite = 1u << 28, kEsdfPar = 1u << 29,
+                   kEsdfInside = 1u << 30;
+constexpr uint32_t kEsdfOffMask = (1u << 27) - 1u;
+struct EsdfDev {
+  uint32_t* st;         // [max_blocks][512] voxel states
+  uint32_t* st2;        // [max_blocks][512] states produced by a face exchange
+  uint32_t* list[2];    // [max_blocks] update sets (current, next)
+  uint32_t* tlist;      // [max_blocks] update set and its face neighbours
+  uint32_t* clist;      // [max_blocks] blocks where a site disappeared
+  uint32_t* stamp_s;    // [max_blocks] generation that put the block in an update set
+  uint32_t* stamp_t;    // [max_blocks] generation that put the block in tlist
+  uint8_t* tchanged;    // [max_blocks] per tlist entry: the exchange changed the block
+  uint32_t* cnt;        // [0], [1] update set sizes, [2] tlist size, [3] clist size
+  unsigned long long* cleared;  // voxels whose parent stopped being a site
+  float site_eps, min_weight;
+  int32_t max_dist;     // voxels, <= 255
 };
 
 // One frame as the kernels see it.  Geometry is anchor-relative: a is the
@@ -125,6 +148,18 @@ __host__ __device__ __forceinline__ uint32_t hash_key(unsigned long long k) {
 }
 
 // Launchers (kernels.cu).
+// Slot of `key` in the hash, or -1 (linear probing, bounded by the table size).
+__device__ __forceinline__ int hash_find(const MapDev& m, unsigned long long key) {
+  uint32_t slot = hash_key(key) & m.cap_mask;
+  for (uint32_t probe = 0; probe <= m.cap_mask; ++probe) {
+    const unsigned long long k = m.keys[slot];
+    if (k == key) return (int)slot;
+    if (k == kEmptyKey) return -1;
+    slot = (slot + 1) & m.cap_mask;
+  }
+  return -1;
+}
+
 template <int NF, int NM>
 cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile_h, cudaStream_t s);
 template <int NF, int NM>
@@ -135,6 +170,15 @@ cudaError_t launch_query(const MapDev& m, const float* pts, int64_t n, float* di
                          cudaStream_t s);
 cudaError_t launch_reset(const MapDev& m, uint32_t cap, cudaStream_t s);
 cudaError_t launch_decay(const MapDev& m, float d_occ, float d_free, cudaStream_t s);
+// ESDF stages (esdf.cu); `cur` selects the current update set.
+cudaError_t launch_esdf_mark(const MapDev& m, const EsdfDev& e, uint32_t gen, cudaStream_t s);
+cudaError_t launch_esdf_clear(const MapDev& m, const EsdfDev& e, uint32_t gen, cudaStream_t s);
+cudaError_t launch_esdf_iteration(const MapDev& m, const EsdfDev& e, int cur, uint32_t gen_t,
+                                  uint32_t gen_next, cudaStream_t s);
+cudaError_t launch_esdf_query(const MapDev& m, const EsdfDev& e, const float* pts, int64_t n,
+                              float* dist, cudaStream_t s);
+cudaError_t launch_import(const MapDev& m, const int32_t* keys, const float* D, const float* W,
+                          int64_t n, cudaStream_t s);
 int integrate_ctas_per_sm(int storage);
 
 }  // namespace gbt

@@ -20,7 +20,7 @@ from . import (BOX, PLANE, SPHERE, outdoor_scene, prim, render_lidar, render_pin
 
 __all__ = ["Frame", "Workload", "pinhole", "lidar64", "config_tiny", "config_room",
            "config_rig", "config_serving_maps", "serving_arrivals", "render_frame",
-           "color_image", "cached"]
+           "color_image", "room_colors", "cached"]
 
 _CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), ".synth_cache")
 
@@ -89,6 +89,16 @@ def color_image(sensor, T, depth, seed: int, frame: int) -> np.ndarray:
     tex = np.where(ok[None], tex, rng.integers(0, 256, size=tex.shape))
     c = np.clip(tex, 0, 255).astype(np.uint32)
     return (c[0] | (c[1] << 8) | (c[2] << 16)).astype(np.uint32)
+
+
+def room_colors(w: Workload, seed: int = 3, use_cache: bool = True) -> np.ndarray:
+    """Colour images (uint32 [n, H, W]) registered to every frame of a
+    pinhole workload, by color_image."""
+    def make():
+        return np.stack([color_image(f.sensor, f.T, f.depth, seed, i)
+                         for i, f in enumerate(w.frames)])
+    key = f"colors:{w.name}:{seed}:{hashlib.sha1(w.frames[0].depth.tobytes()).hexdigest()[:12]}"
+    return cached(key, make) if use_cache else make()
 
 
 def cached(key: str, fn):

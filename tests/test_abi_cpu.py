@@ -40,15 +40,17 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(gt.Pinhole) == 24
     assert ctypes.sizeof(gt.Lidar) == 28
     assert ctypes.sizeof(gt.MapOpts) == 64
+    assert ctypes.sizeof(gt.EsdfOpts) == 12
     assert ctypes.sizeof(gt.FrameDesc) == 4 + 4 + 24 + 28 + 4 + 8 + 128 + 8
 
 
 def test_header_compiles_as_c_and_layouts_agree(tmp_path):
     prog = tmp_path / "layout.c"
     prog.write_text('#include "tsdf.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(tsdf_pinhole),'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(tsdf_pinhole),'
                     ' sizeof(tsdf_lidar), sizeof(tsdf_map_opts), sizeof(tsdf_frame_desc),'
-                    ' offsetof(tsdf_frame_desc, depth_dev), offsetof(tsdf_frame_desc, color_dev)); return 0;}\n')
+                    ' offsetof(tsdf_frame_desc, depth_dev), offsetof(tsdf_frame_desc, color_dev),'
+                    ' sizeof(tsdf_esdf_opts)); return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
                     str(prog), "-o", str(exe)], check=True)
@@ -56,4 +58,4 @@ def test_header_compiles_as_c_and_layouts_agree(tmp_path):
                                            check=True).stdout.split()]
     assert vals == [ctypes.sizeof(gt.Pinhole), ctypes.sizeof(gt.Lidar), ctypes.sizeof(gt.MapOpts),
                     ctypes.sizeof(gt.FrameDesc), gt.FrameDesc.depth_dev.offset,
-                    gt.FrameDesc.color_dev.offset]
+                    gt.FrameDesc.color_dev.offset, ctypes.sizeof(gt.EsdfOpts)]
