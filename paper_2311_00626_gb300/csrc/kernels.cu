@@ -21,6 +21,7 @@
 //
 // Discrete decisions use explicit round-to-nearest intrinsics in a fixed
 // order (no contraction) so that they are reproducible on a CPU.
+#include <algorithm>
 #include <cfloat>
 
 #include "tsdf_internal.cuh"
@@ -424,12 +425,19 @@ __device__ __forceinline__ float weight(const MapDev& m, float dv, float dp) {
 // the TSDF average, or for an occupancy layer (Sec. IV-B, second functor)
 // the running addition of l_free in front of the surface (d_p > 0) and
 // l_occ otherwise.
-template <int STORAGE>
+// WEIGHTED: the map uses a non-constant weighting function (the constant
+// weight 1 keeps the update short: fewer instructions in the unrolled loops).
+template <int STORAGE, bool WEIGHTED>
 __device__ __forceinline__ void apply(const MapDev& m, float& D, float& W, float dv, float dp) {
-  if (STORAGE == kStorageOcc)
+  if (STORAGE == kStorageOcc) {
     D += dp > 0.0f ? m.l_free : m.l_occ;
-  else
-    fuse(D, W, fminf(dp, m.tau), m.weighting ? weight(m, dv, dp) : 1.0f, m.wmax);
+  } else if (WEIGHTED) {
+    fuse(D, W, fminf(dp, m.tau), weight(m, dv, dp), m.wmax);
+  } else {
+    const float wn = W + 1.0f;
+    D = D + __fdividef(fminf(dp, m.tau) - D, wn);
+    W = fminf(wn, m.wmax);
+  }
 }
 
 // Colour functor: the running average of the pixel's r, g, b with weight 1
@@ -557,7 +565,7 @@ __device__ __forceinline__ void row_points(const FrameDev& F, float v, const Vox
 // order.  An out-of-image projection reads no pixel and yields d = 0, which
 // is invalid like a missing depth.  A colour layer updates only voxels within
 // tau of the surface on both sides.
-template <int NQ, int STORAGE, class P>
+template <int NQ, int STORAGE, bool WEIGHTED, class P>
 __device__ __forceinline__ void fuse_pinhole(const P& p, const int (&fq)[4], const MapDev& m,
                                              const VoxelRow& r, float* D, float* W, float* G,
                                              float* B, unsigned long long& upd) {
@@ -594,7 +602,7 @@ __device__ __forceinline__ void fuse_pinhole(const P& p, const int (&fq)[4], con
           if (dp > m.tau) continue;
           apply_color(m, D[i], G[i], B[i], W[i], c[q][i]);
         } else {
-          apply<STORAGE>(m, D[i], W[i], z[q][i], dp);
+          apply<STORAGE, WEIGHTED>(m, D[i], W[i], z[q][i], dp);
         }
         ++upd;
       }
@@ -603,7 +611,7 @@ __device__ __forceinline__ void fuse_pinhole(const P& p, const int (&fq)[4], con
 
 // One frame of any sensor kind, voxel by voxel (colour layers take pinhole
 // frames only, through fuse_pinhole).
-template <int STORAGE>
+template <int STORAGE, bool WEIGHTED>
 __device__ __forceinline__ void fuse_any(const FrameDev& F, const MapDev& m, const VoxelRow& r,
                                          float* D, float* W, unsigned long long& upd) {
   if (STORAGE == kStorageColor) return;
@@ -615,12 +623,12 @@ __device__ __forceinline__ void fuse_any(const FrameDev& F, const MapDev& m, con
     if (!sample(F, m, px[i], py[i], pz[i], d, dv)) continue;
     const float dp = __fsub_rn(d, dv);
     if (dp < -m.tau) continue;
-    apply<STORAGE>(m, D[i], W[i], dv, dp);
+    apply<STORAGE, WEIGHTED>(m, D[i], W[i], dv, dp);
     ++upd;
   }
 }
 
-template <int NF, int NM, int STORAGE, bool PINHOLE_ONLY>
+template <int NF, int NM, int STORAGE, bool PINHOLE_ONLY, bool WEIGHTED>
 __global__ void __launch_bounds__(kIntegrateThreads)
     integrate_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
   __shared__ uint32_t s_begin[NM + 1];
@@ -694,17 +702,18 @@ __global__ void __launch_bounds__(kIntegrateThreads)
             }
           }
         }
-        if (nq == 4) fuse_pinhole<4, STORAGE>(p, fq, m, vr, D, W, G, B, my_upd);
+        if (nq == 4) fuse_pinhole<4, STORAGE, WEIGHTED>(p, fq, m, vr, D, W, G, B, my_upd);
         else if (nq >= 1) {
           for (int q = 0; q < nq; ++q) {
-            const int fq1[4] = {fq[q], -1, -1, -1};
-            fuse_pinhole<1, STORAGE>(p, fq1, m, vr, D, W, G, B, my_upd);
+            // selects instead of fq[q]: a dynamic index would put fq in local memory
+            const int fq1[4] = {q == 0 ? fq[0] : (q == 1 ? fq[1] : fq[2]), -1, -1, -1};
+            fuse_pinhole<1, STORAGE, WEIGHTED>(p, fq1, m, vr, D, W, G, B, my_upd);
           }
         }
         else if (!PINHOLE_ONLY) {
           const int f = __ffs(bits) - 1;  // a LiDAR frame
           bits &= bits - 1u;
-          fuse_any<STORAGE>(p.fr[f], m, vr, D, W, my_upd);
+          fuse_any<STORAGE, WEIGHTED>(p.fr[f], m, vr, D, W, my_upd);
         }
       }
       Voxels4<STORAGE>::store(m, pool, t, D, W, G, B);
@@ -860,20 +869,29 @@ cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStrea
   // colour maps take pinhole frames only (checked by the host API)
   const bool ph = pinhole_only(p);
   const int st = p.maps[0].storage;
+  // the weighted update with weighting 0 is the constant-weight update, so
+  // one weighted map selects the weighted kernel for the whole batch
+  bool wt = false;
+  for (int k = 0; k < p.n_maps; ++k) wt = wt || p.maps[k].weighting != 0;
+  const dim3 g(n_ctas), b(kIntegrateThreads);
   if (st == kStorageColor)
-    integrate_kernel<NF, NM, kStorageColor, true><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+    integrate_kernel<NF, NM, kStorageColor, true, false><<<g, b, 0, s>>>(p);
   else if (st == kStorageOcc && ph)
-    integrate_kernel<NF, NM, kStorageOcc, true><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+    integrate_kernel<NF, NM, kStorageOcc, true, false><<<g, b, 0, s>>>(p);
   else if (st == kStorageOcc)
-    integrate_kernel<NF, NM, kStorageOcc, false><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+    integrate_kernel<NF, NM, kStorageOcc, false, false><<<g, b, 0, s>>>(p);
+  else if (st == kStorageF16 && wt)
+    integrate_kernel<NF, NM, kStorageF16, false, true><<<g, b, 0, s>>>(p);
   else if (st == kStorageF16 && ph)
-    integrate_kernel<NF, NM, kStorageF16, true><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+    integrate_kernel<NF, NM, kStorageF16, true, false><<<g, b, 0, s>>>(p);
   else if (st == kStorageF16)
-    integrate_kernel<NF, NM, kStorageF16, false><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+    integrate_kernel<NF, NM, kStorageF16, false, false><<<g, b, 0, s>>>(p);
+  else if (wt)
+    integrate_kernel<NF, NM, kStorageF32, false, true><<<g, b, 0, s>>>(p);
   else if (ph)
-    integrate_kernel<NF, NM, kStorageF32, true><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+    integrate_kernel<NF, NM, kStorageF32, true, false><<<g, b, 0, s>>>(p);
   else
-    integrate_kernel<NF, NM, kStorageF32, false><<<n_ctas, kIntegrateThreads, 0, s>>>(p);
+    integrate_kernel<NF, NM, kStorageF32, false, false><<<g, b, 0, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -923,23 +941,35 @@ cudaError_t launch_reset(const MapDev& m, uint32_t cap, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-int integrate_ctas_per_sm(int storage) {
+namespace {
+template <class K>
+int occupancy(K kernel) {
   int n = 0;
-  cudaError_t e;
-  if (storage == kStorageColor)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageColor, true>, kIntegrateThreads, 0);
-  else if (storage == kStorageOcc)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageOcc, false>, kIntegrateThreads, 0);
-  else if (storage == kStorageF16)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageF16, false>, kIntegrateThreads, 0);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &n, integrate_kernel<kMaxFrames, kMaxMaps, kStorageF32, false>, kIntegrateThreads, 0);
-  if (e != cudaSuccess || n <= 0) n = 4;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kIntegrateThreads, 0) != cudaSuccess)
+    n = 0;
   return n;
+}
+}  // namespace
+
+// Resident integration CTAs per SM: the smallest over the kernel variants a
+// map of this storage can launch (the grid is persistent).
+int integrate_ctas_per_sm(int storage) {
+  constexpr int F = kMaxFrames, M = kMaxMaps;
+  int n;
+  if (storage == kStorageColor)
+    n = occupancy(integrate_kernel<F, M, kStorageColor, true, false>);
+  else if (storage == kStorageOcc)
+    n = std::min(occupancy(integrate_kernel<F, M, kStorageOcc, true, false>),
+                 occupancy(integrate_kernel<F, M, kStorageOcc, false, false>));
+  else if (storage == kStorageF16)
+    n = std::min({occupancy(integrate_kernel<F, M, kStorageF16, true, false>),
+                  occupancy(integrate_kernel<F, M, kStorageF16, false, false>),
+                  occupancy(integrate_kernel<F, M, kStorageF16, false, true>)});
+  else
+    n = std::min({occupancy(integrate_kernel<F, M, kStorageF32, true, false>),
+                  occupancy(integrate_kernel<F, M, kStorageF32, false, false>),
+                  occupancy(integrate_kernel<F, M, kStorageF32, false, true>)});
+  return n > 0 ? n : 4;
 }
 
 }  // namespace gbt
