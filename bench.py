@@ -292,6 +292,12 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # walk statistics (band segments and cells, for the allocator's roofline)
+    # from one extra untimed step: counting them costs about 5 %
+    gt.map_walk_stats(m.handle, True)
+    step()
+    walk = m.stats()
+    gt.map_walk_stats(m.handle, False)
     st = m.stats()
     updates_per_step = st["voxel_updates"]
     clocks = ClockSampler(local)
@@ -316,7 +322,7 @@ def main():
     achieved = integ_bytes_per_launch / (integ_ms_per_launch * 1e-3) / 1e9
     # allocation kernel, ALU roofline: algorithmic operations of its walks
     alloc_ms_per_launch = alloc_ms / max(calls, 1)
-    alloc_ops_per_launch = (OPS_PER_SEGMENT * st["segments"] + OPS_PER_CELL * st["cells"]) / launches_per_step
+    alloc_ops_per_launch = (OPS_PER_SEGMENT * walk["segments"] + OPS_PER_CELL * walk["cells"]) / launches_per_step
     alloc_achieved = alloc_ops_per_launch / (alloc_ms_per_launch * 1e-3)
     alloc_share = alloc_ms / max(alloc_ms + integ_ms, 1e-9)
     value = aggregate_rate(updates_per_step, ms, ws)
@@ -404,6 +410,30 @@ def main():
             "frames_per_s": ws * n_frames / (ms4 * 1e-3)}
         m4.close()
         del colors
+        # ESDF (Sec. IV-C) of the room map: built from all 300 frames, then
+        # brought up to date after 10 more frames (incremental)
+        m5 = gt.TsdfMap(w.voxel_size, w.truncation_voxels, w.max_weight)
+        make_step(m5, args.batch)()
+        v32 = float(np.float32(w.voxel_size))
+
+        def esdf_ms(fn):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b)
+        full_ms = esdf_ms(lambda: m5.esdf_update(v32, 1e-4, 64))
+        full_stats = m5.esdf_stats()
+        descs5 = [gt.frame_desc(0, f.sensor, f.T, d) for f, d in zip(w.frames[:10], frames_dev[:10])]
+        gt.integrate_batch([m5.handle], descs5)
+        inc_ms = esdf_ms(lambda: m5.esdf_update(v32, 1e-4, 64))
+        inc_stats = {k: v - full_stats[k] for k, v in m5.esdf_stats().items()}
+        forms["esdf"] = {"blocks": m5.stats()["blocks"], "site_eps_m": v32, "max_dist_vox": 64,
+                         "full_ms": full_ms, "full": full_stats,
+                         "incremental_after_10_frames_ms": inc_ms, "incremental": inc_stats}
+        m5.close()
         forms["fp32_batched_speedup_vs_one_frame"] = ms1 / ms
         forms["fp16_batched_speedup_vs_one_frame"] = ms1 / ms2
 
@@ -430,7 +460,7 @@ def main():
                          "peak_source": "152 SMs x 128 lanes x 2070 MHz",
                          "ops_per_launch": alloc_ops_per_launch,
                          "ms_per_launch": alloc_ms_per_launch,
-                         "segments_per_step": st["segments"], "cells_per_step": st["cells"]},
+                         "segments_per_step": walk["segments"], "cells_per_step": walk["cells"]},
             "roofline_integrate": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                                    "unit": "GB/s", "frac": achieved / hbm_peak,
                                    "traffic": _traffic("integrate_kernel"),

@@ -235,8 +235,15 @@ tsdf_status map_num_blocks(const tsdf_map* map, int64_t* out);
  * status bits, out[4] block visits (blocks listed by integration launches,
  * summed over launches), out[5] integration launches, out[6] band segments
  * walked (valid pixels), out[7] block-grid cells emitted by those walks
- * (counting a block once per pixel that meets it). */
+ * (counting a block once per pixel that meets it); out[6] and out[7] count
+ * only while map_walk_stats is enabled. */
 tsdf_status map_stats(const tsdf_map* map, int64_t out[8]);
+
+/* map_walk_stats — diagnostics: while enabled, allocation launches that
+ * include this map count band segments and walked block-grid cells into
+ * map_stats out[6] and out[7] (off by default: it costs about 5 % of the
+ * allocation time). */
+tsdf_status map_walk_stats(tsdf_map* map, int32_t enable);
 
 /* map_timing — diagnostics: while enabled, every integrate call on this map
  * (or integrate_batch sub-batch whose first map it is) records CUDA events

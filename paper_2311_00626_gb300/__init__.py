@@ -25,7 +25,7 @@ __all__ = ["TsdfError", "Pinhole", "Lidar", "MapOpts", "FrameDesc", "TsdfMap", "
            "LAYER_OCCUPANCY", "LAYER_COLOR", "STORAGE_FP32", "STORAGE_FP16",
            "integrate_color", "query_color", "map_export_color", "map_decay_occupancy",
            "EsdfOpts", "map_import", "map_esdf_update", "map_esdf_export", "map_esdf_query",
-           "map_esdf_stats",
+           "map_esdf_stats", "map_walk_stats",
            "SENSOR_PINHOLE", "SENSOR_LIDAR", "EXPORTED_SYMBOLS"]
 
 STORAGE_FP32, STORAGE_FP16 = 0, 1
@@ -40,7 +40,7 @@ EXPORTED_SYMBOLS = ["map_create", "map_create_ex", "integrate_depth", "integrate
                     "map_export", "map_reset", "map_destroy", "map_timing", "map_kernel_times",
                     "integrate_depth_static", "integrate_color", "query_color",
                     "map_export_color", "map_decay_occupancy", "map_import", "map_esdf_update",
-                    "map_esdf_export", "map_esdf_query", "map_esdf_stats"]
+                    "map_esdf_export", "map_esdf_query", "map_esdf_stats", "map_walk_stats"]
 
 
 class TsdfError(RuntimeError):
@@ -118,6 +118,7 @@ def lib():
                 "map_reset": ([P, P], I),
                 "map_destroy": ([P], I),
                 "map_timing": ([P, I], I),
+                "map_walk_stats": ([P, I], I),
                 "map_kernel_times": ([P, P, ctypes.POINTER(ctypes.c_int64)], I),
                 "integrate_depth_static": ([ctypes.POINTER(MapBuffers), F, I, F, P,
                                             ctypes.POINTER(Pinhole), P, P], I),
@@ -249,6 +250,11 @@ def map_stats(m: int) -> dict:
     return {"blocks": int(out[0]), "voxel_updates": int(out[1]), "frames": int(out[2]),
             "status_bits": int(out[3]), "block_visits": int(out[4]), "launches": int(out[5]),
             "segments": int(out[6]), "cells": int(out[7])}
+
+
+def map_walk_stats(m: int, enable: bool = True):
+    """Count band segments and walked cells (map_stats "segments", "cells")."""
+    _check(lib().map_walk_stats(m, int(enable)), "map_walk_stats")
 
 
 def map_timing(m: int, enable: bool = True):

@@ -214,8 +214,9 @@ __device__ __forceinline__ bool pixel_segment(const FrameDev& F, const MapDev& m
 // CTA-local set; then the tile's distinct blocks are claimed in the global
 // hash.  Segments that start far from the sensor's block count cells from
 // their own start cell and claim their blocks directly.  PINHOLE_ONLY: every
-// frame of the batch is a pinhole camera (the LiDAR code is left out).
-template <int NF, int NM, int TH, bool PINHOLE_ONLY>
+// frame of the batch is a pinhole camera (the LiDAR code is left out);
+// STATS: count band segments and walked cells (a diagnostic, 5 % slower).
+template <int NF, int NM, int TH, bool PINHOLE_ONLY, bool STATS>
 __global__ void __launch_bounds__(kAllocThreads)
     band_alloc_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
   constexpr int kRows = TH * kTileW / kAllocThreads;  // pixel rows per thread
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(kAllocThreads)
   __syncthreads();
   const uint32_t nk = s_nkeys;
   for (uint32_t i = threadIdx.x; i < nk; i += kAllocThreads) claim_block(m, rel_to_key(s_keys[i], F.a), F.bit);
-  if (m.walk_stats) {
+  if (STATS) {
     for (int o = 16; o > 0; o >>= 1) {
       segs += __shfl_down_sync(0xffffffffu, segs, o);
       cells += __shfl_down_sync(0xffffffffu, cells, o);
@@ -682,14 +683,14 @@ __global__ void __launch_bounds__(kIntegrateThreads)
       uint32_t bits = slot_mask;
       while (bits) {
         // bit k of the mask is frame k of the batch; frames apply in batch
-        // order.  A run of four pinhole frames issues all its depth loads
-        // before the first update; shorter runs go frame by frame (fewer
-        // code paths keep the kernel small in the instruction cache).
+        // order.  Two consecutive pinhole frames issue all their depth loads
+        // before the first update (longer runs measured slower: the unrolled
+        // code outgrows the instruction cache).
         int fq[4];
         int nq = 0;
         bool go = true;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 2; ++q) {
           fq[q] = -1;
           if (go && bits) {
             const int f = __ffs(bits) - 1;
@@ -702,14 +703,9 @@ __global__ void __launch_bounds__(kIntegrateThreads)
             }
           }
         }
-        if (nq == 4) fuse_pinhole<4, STORAGE, WEIGHTED>(p, fq, m, vr, D, W, G, B, my_upd);
-        else if (nq >= 1) {
-          for (int q = 0; q < nq; ++q) {
-            // selects instead of fq[q]: a dynamic index would put fq in local memory
-            const int fq1[4] = {q == 0 ? fq[0] : (q == 1 ? fq[1] : fq[2]), -1, -1, -1};
-            fuse_pinhole<1, STORAGE, WEIGHTED>(p, fq1, m, vr, D, W, G, B, my_upd);
-          }
-        }
+        fq[2] = fq[3] = -1;
+        if (nq == 2) fuse_pinhole<2, STORAGE, WEIGHTED>(p, fq, m, vr, D, W, G, B, my_upd);
+        else if (nq == 1) fuse_pinhole<1, STORAGE, WEIGHTED>(p, fq, m, vr, D, W, G, B, my_upd);
         else if (!PINHOLE_ONLY) {
           const int f = __ffs(bits) - 1;  // a LiDAR frame
           bits &= bits - 1u;
@@ -852,14 +848,23 @@ template <int NF, int NM>
 cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile_h, cudaStream_t s) {
   if (n_ctas <= 0) return cudaSuccess;
   const bool ph = pinhole_only(p);
-  if (tile_h == kTileHBig && ph)
-    band_alloc_kernel<NF, NM, kTileHBig, true><<<n_ctas, kAllocThreads, 0, s>>>(p);
-  else if (tile_h == kTileHBig)
-    band_alloc_kernel<NF, NM, kTileHBig, false><<<n_ctas, kAllocThreads, 0, s>>>(p);
-  else if (ph)
-    band_alloc_kernel<NF, NM, kTileHSmall, true><<<n_ctas, kAllocThreads, 0, s>>>(p);
-  else
-    band_alloc_kernel<NF, NM, kTileHSmall, false><<<n_ctas, kAllocThreads, 0, s>>>(p);
+  bool st = false;
+  for (int k = 0; k < p.n_maps; ++k) st = st || p.maps[k].walk_stats != 0;
+  const dim3 g(n_ctas), b(kAllocThreads);
+  if (st) {  // diagnostics: one generic variant per tile height
+    if (tile_h == kTileHBig)
+      band_alloc_kernel<NF, NM, kTileHBig, false, true><<<g, b, 0, s>>>(p);
+    else
+      band_alloc_kernel<NF, NM, kTileHSmall, false, true><<<g, b, 0, s>>>(p);
+  } else if (tile_h == kTileHBig && ph) {
+    band_alloc_kernel<NF, NM, kTileHBig, true, false><<<g, b, 0, s>>>(p);
+  } else if (tile_h == kTileHBig) {
+    band_alloc_kernel<NF, NM, kTileHBig, false, false><<<g, b, 0, s>>>(p);
+  } else if (ph) {
+    band_alloc_kernel<NF, NM, kTileHSmall, true, false><<<g, b, 0, s>>>(p);
+  } else {
+    band_alloc_kernel<NF, NM, kTileHSmall, false, false><<<g, b, 0, s>>>(p);
+  }
   return cudaGetLastError();
 }
 

@@ -384,7 +384,7 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   d.list_cap = (uint32_t)o.max_blocks;
   d.storage = o.storage;
   d.lidar_nearest = o.lidar_nearest ? 1 : 0;
-  d.walk_stats = 1;
+  d.walk_stats = 0;
   d.v = voxel_size;
   d.tau = (float)((double)truncation_voxels * m->vd);
   d.inv_tau = 1.0f / d.tau;
@@ -582,6 +582,12 @@ tsdf_status map_stats(const tsdf_map* map, int64_t out[8]) {
   out[5] = (int64_t)c[gbt::kCntLaunches];
   out[6] = (int64_t)c[gbt::kCntSegments];
   out[7] = (int64_t)c[gbt::kCntCells];
+  return TSDF_OK;
+}
+
+tsdf_status map_walk_stats(tsdf_map* map, int32_t enable) {
+  if (!map) return TSDF_ERR_ARG;
+  map->dev.walk_stats = enable ? 1 : 0;
   return TSDF_OK;
 }
 

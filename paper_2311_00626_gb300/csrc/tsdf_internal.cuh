@@ -57,7 +57,7 @@ struct MapDev {
   unsigned long long* block_keys; // [max_blocks] key of each pool block
   unsigned long long* counters;   // [kNumCounters]; entries from kCntSegments on only
                                   // when walk_stats != 0
-  int32_t walk_stats;             // count band segments and cells
+  int32_t walk_stats;             // count band segments and cells (diagnostic)
   uint32_t* list;                 // [list_cap] slots met by the current batch
   unsigned int* ctl;              // [0] list length, [1] finished integration CTAs,
                                   // [2] entries handed out (first map of a batch)

@@ -40,6 +40,7 @@ def run_gpu(frames, voxel_size, trunc=4, wmax=100.0, storage=0, batch=1, lidar_n
                                         "l_free": occupancy[1]}
     m = gt.TsdfMap(voxel_size, trunc, wmax, storage=storage, max_blocks=max_blocks,
                    lidar_nearest=lidar_nearest, lidar_guard=guard, weighting=weighting, **occ)
+    gt.map_walk_stats(m.handle, True)  # the tests compare walked cells with the oracle's
     dev = to_device(frames)
     if batch == 1:
         for f, d in zip(frames, dev):
