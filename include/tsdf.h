@@ -273,7 +273,7 @@ tsdf_status map_export_color(const tsdf_map* map, int32_t* keys_host, float* rgb
                              float* weight_host, int64_t n);
 
 /*
- * map_decay_occupancy — one decay step of an occupancy layer (Sec. VI: the
+ * map_decay_occupancy — one decay step of an occupancy layer (Sec. V-E: the
  * dynamic part of a scene, kept in its own occupancy layer, fades over
  * time; the paper gives no rule): every allocated voxel's log-odds moves
  * toward 0 (probability 1/2), occupied values (> 0) by decay_occ, free

@@ -1,8 +1,9 @@
 """CPU oracle for projective TSDF integration — TEST INFRASTRUCTURE ONLY.
 
 A plain FP64 restatement of nvblox's frame integration (Sec. IV-B, Eq. 1-3)
-in ``tsdf_oracle.cpp`` and of its incremental ESDF (Sec. IV-C) in
-``esdf_oracle.cpp``, loaded through ctypes.  Only the test suite, the
+in ``tsdf_oracle.cpp``, of its incremental ESDF (Sec. IV-C) in
+``esdf_oracle.cpp`` and of marching-cubes meshing in ``mesh_oracle.cpp``,
+loaded through ctypes.  Only the test suite, the
 package smoke check and the benchmark's CPU-baseline leg may import this
 module; the product path never does, and it shares no code with the CUDA
 path.  See the header of ``tsdf_oracle.cpp`` for the precision contract
@@ -18,7 +19,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "tsdf_oracle.cpp"), os.path.join(_HERE, "esdf_oracle.cpp")]
+_SRCS = [os.path.join(_HERE, f) for f in ("tsdf_oracle.cpp", "esdf_oracle.cpp", "mesh_oracle.cpp")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -83,6 +84,10 @@ def _load():
             lib.esdf_orc_export.argtypes = [P, P, P, L]
             lib.esdf_orc_export.restype = L
             lib.esdf_orc_counters.argtypes = [P, P]
+            lib.mesh_orc_extract.argtypes = [P, P, P, L, P, F, F, P, P, P, L]
+            lib.mesh_orc_extract.restype = L
+            lib.mesh_orc_case.argtypes = [I, P]
+            lib.mesh_orc_case.restype = I
             _lib = lib
             del D
     return _lib
@@ -264,3 +269,33 @@ class EsdfOracle:
         out = np.zeros(4, np.int64)
         self._lib.esdf_orc_counters(self._h, _p(out))
         return dict(zip(["iterations", "swept", "pulled", "cleared"], (int(x) for x in out)))
+
+
+def mesh_extract(keys, D, W, voxel_size: float, min_weight: float = 1e-4, blocks=None):
+    """Marching-cubes triangles of the cubes of `blocks` (bool [n], default
+    all): (cube int32 [t,3] = voxel index of its corner 0, vertex keys int32
+    [t,3,4] = lower-corner voxel index and edge axis, positions float64
+    [t,3,3] in metres)."""
+    keys = np.ascontiguousarray(keys, np.int32)
+    D = np.ascontiguousarray(D, np.float32)
+    W = np.ascontiguousarray(W, np.float32)
+    n = len(keys)
+    sel = np.ones(n, np.uint8) if blocks is None else np.ascontiguousarray(blocks, np.uint8)
+    lib = _load()
+    cap = 1 << 16
+    while True:
+        cube = np.zeros((cap, 3), np.int32)
+        k = np.zeros((cap, 3, 4), np.int32)
+        pos = np.zeros((cap, 3, 3), np.float64)
+        t = int(lib.mesh_orc_extract(_p(keys), _p(D), _p(W), n, _p(sel), voxel_size, min_weight,
+                                     _p(cube), _p(k), _p(pos), cap))
+        if t <= cap:
+            return cube[:t], k[:t], pos[:t]
+        cap = t
+
+
+def mesh_case(inside_mask: int) -> np.ndarray:
+    """Triangles (edge numbers, int32 [t,3]) of one cube configuration."""
+    e = np.zeros(36, np.int32)
+    t = int(_load().mesh_orc_case(inside_mask, _p(e)))
+    return e[:3 * t].reshape(t, 3)

@@ -20,7 +20,7 @@
  *     weights added up to max_weight (Sec. IV-B);
  *   - occupancy layer (Sec. IV-B, second functor), optional: the same voxels
  *     instead add a constant log-odds, negative in front of the surface
- *     (d_p > 0), positive otherwise; a decay step (Sec. VI: dynamic content
+ *     (d_p > 0), positive otherwise; a decay step (Sec. V-E: dynamic content
  *     of an occupancy layer fades over time) moves every voxel's log-odds
  *     toward 0 by a fixed amount without crossing 0.
  *
@@ -296,7 +296,7 @@ inline void occupancy_update(double& L, double& N, bool in_front, double l_occ, 
   N += 1.0;
 }
 
-/* Occupancy decay (Sec. VI, the paper gives no rule): log-odds above 0
+/* Occupancy decay (Sec. V-E, the paper gives no rule): log-odds above 0
  * (occupied) drop by decay_occ, log-odds below 0 (free) rise by decay_free,
  * neither crossing 0, so every voxel drifts back to the prior p = 0.5. */
 inline void occupancy_decay(double& L, double decay_occ, double decay_free) {

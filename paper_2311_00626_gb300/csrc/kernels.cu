@@ -17,7 +17,7 @@
 //                     batch.
 //  query_kernel,      point -> voxel lookup through the hash.
 //  query_color_kernel
-//  decay_kernel       occupancy decay over every allocated block (Sec. VI).
+//  decay_kernel       occupancy decay over every allocated block (Sec. V-E).
 //
 // Discrete decisions use explicit round-to-nearest intrinsics in a fixed
 // order (no contraction) so that they are reproducible on a CPU.

@@ -5,7 +5,7 @@ Scenes, trajectories and depth / range images are produced by ``synth.c``
 of the integration method; the oracle tests and the CUDA path's tests and
 benchmark both draw their inputs from this module.
 
-The workload recipes mirror the shapes of the paper's evaluation (Sec. VI:
+The workload recipes mirror the shapes of the paper's evaluation (Sec. V:
 indoor RGB-D rooms, a 64-beam spinning LiDAR) with seeded stand-ins for the
 datasets, which are not available here.
 """

@@ -3,7 +3,7 @@
 Each recipe returns plain numpy data: sensor intrinsics as dicts, camera- or
 LiDAR-to-world poses as (4, 4) float64 arrays and depth / range images as
 float32 arrays.  The recipes are the stand-ins for the paper's datasets
-(Replica / Redwood RGB-D rooms, a 64-beam spinning LiDAR; Sec. VI) and carry
+(Replica / Redwood RGB-D rooms, a 64-beam spinning LiDAR; Sec. V) and carry
 the sizes of the paper's workloads at the resolutions used here.
 """
 from __future__ import annotations

@@ -461,7 +461,7 @@ def _decayed(L, k, d_occ, d_free):
 
 
 def test_occupancy_decay_closed_form():
-    """Occupancy decay (Sec. VI: dynamic content of an occupancy layer fades):
+    """Occupancy decay (Sec. V-E: dynamic content of an occupancy layer fades):
     after the two-plane sequence of the closed-form test above, k decay
     steps move occupied log-odds down by k * d_occ and free ones up by
     k * d_free, neither crossing 0; update counts are kept.  Checked after 3

@@ -376,7 +376,7 @@ def test_occupancy_lidar():
 
 
 def test_occupancy_decay_interleaved():
-    """Occupancy decay (Sec. VI) interleaved with integration: 10 room frames,
+    """Occupancy decay (Sec. V-E) interleaved with integration: 10 room frames,
     2 decay steps, 10 more frames, 3 steps, against the oracle doing the
     same; the log-odds carry the FP32 error of a running sum of 25 terms."""
     import oracle
