@@ -348,6 +348,28 @@ tsdf_status map_esdf_query(const tsdf_map* map, const float* pts_dev, int64_t n,
  * exchanges, out[3] voxels whose parent was cleared.  Synchronises. */
 tsdf_status map_esdf_stats(const tsdf_map* map, int64_t out[4]);
 
+/*
+ * map_mesh — marching-cubes triangles of the map's TSDF (Sec. IV-B: updated
+ * blocks are meshed with a parallel Marching Cubes).  A cube joins the
+ * voxel centres g .. g + (1, 1, 1) and belongs to the block of g; it is
+ * meshed if its eight voxels exist and have W >= min_weight.  A corner is
+ * inside if D < 0; a vertex sits on each edge whose ends differ, at
+ * t = D_lo / (D_lo - D_hi) from the lower end.  Faces with two diagonal
+ * inside corners keep those corners apart, so neighbouring cubes join
+ * without gaps; triangles face the outside (increasing D).  changed_only:
+ * only the blocks changed since the previous call and the blocks whose
+ * cubes reach into them, else every block.  Output (device): tri_pos_dev
+ * float32 [cap][3][3] vertex positions (m); tri_keys_dev int32 [cap][3][4]
+ * (may be NULL) the global voxel index of each vertex's lower edge end and
+ * the edge axis; tri_cube_dev int32 [cap][3] (may be NULL) the cube's voxel
+ * index.  Triangle order is unspecified.  *n_tris = triangles produced;
+ * TSDF_ERR_CAPACITY if more than cap (the first cap are written).  TSDF
+ * maps only.  Synchronises cuda_stream.
+ */
+tsdf_status map_mesh(tsdf_map* map, float min_weight, int32_t changed_only, float* tri_pos_dev,
+                     int32_t* tri_keys_dev, int32_t* tri_cube_dev, int64_t cap, int64_t* n_tris,
+                     void* cuda_stream);
+
 /* map_reset — drop every block (keeps the allocation), enqueued on
  * cuda_stream; clears the sticky status. */
 tsdf_status map_reset(tsdf_map* map, void* cuda_stream);

@@ -25,7 +25,7 @@ __all__ = ["TsdfError", "Pinhole", "Lidar", "MapOpts", "FrameDesc", "TsdfMap", "
            "LAYER_OCCUPANCY", "LAYER_COLOR", "STORAGE_FP32", "STORAGE_FP16",
            "integrate_color", "query_color", "map_export_color", "map_decay_occupancy",
            "EsdfOpts", "map_import", "map_esdf_update", "map_esdf_export", "map_esdf_query",
-           "map_esdf_stats", "map_walk_stats",
+           "map_esdf_stats", "map_walk_stats", "map_mesh",
            "SENSOR_PINHOLE", "SENSOR_LIDAR", "EXPORTED_SYMBOLS"]
 
 STORAGE_FP32, STORAGE_FP16 = 0, 1
@@ -40,7 +40,8 @@ EXPORTED_SYMBOLS = ["map_create", "map_create_ex", "integrate_depth", "integrate
                     "map_export", "map_reset", "map_destroy", "map_timing", "map_kernel_times",
                     "integrate_depth_static", "integrate_color", "query_color",
                     "map_export_color", "map_decay_occupancy", "map_import", "map_esdf_update",
-                    "map_esdf_export", "map_esdf_query", "map_esdf_stats", "map_walk_stats"]
+                    "map_esdf_export", "map_esdf_query", "map_esdf_stats", "map_walk_stats",
+                    "map_mesh"]
 
 
 class TsdfError(RuntimeError):
@@ -119,6 +120,7 @@ def lib():
                 "map_destroy": ([P], I),
                 "map_timing": ([P, I], I),
                 "map_walk_stats": ([P, I], I),
+                "map_mesh": ([P, F, I, P, P, P, L64, ctypes.POINTER(ctypes.c_int64), P], I),
                 "map_kernel_times": ([P, P, ctypes.POINTER(ctypes.c_int64)], I),
                 "integrate_depth_static": ([ctypes.POINTER(MapBuffers), F, I, F, P,
                                             ctypes.POINTER(Pinhole), P, P], I),
@@ -335,6 +337,31 @@ def map_esdf_stats(m: int) -> dict:
     return dict(zip(["iterations", "swept", "pulled", "cleared"], (int(x) for x in out)))
 
 
+def map_mesh(m: int, min_weight: float = 1e-4, changed_only: bool = False, with_keys: bool = True,
+             cap: int = 0, stream=None):
+    """Marching-cubes triangles: (pos float32 [t,3,3], keys int32 [t,3,4] or
+    None, cube int32 [t,3] or None) as CUDA tensors.  When cap is too small
+    a full extraction is retried with room for all triangles; a changed_only
+    extraction raises (its changed blocks were consumed)."""
+    import torch
+    cap = cap or (1 << 20)
+    n = ctypes.c_int64()
+    while True:
+        pos = torch.empty((cap, 3, 3), dtype=torch.float32, device="cuda")
+        keys = torch.empty((cap, 3, 4), dtype=torch.int32, device="cuda") if with_keys else None
+        cube = torch.empty((cap, 3), dtype=torch.int32, device="cuda") if with_keys else None
+        code = lib().map_mesh(m, min_weight, int(changed_only), _dptr(pos),
+                              _dptr(keys) if keys is not None else None,
+                              _dptr(cube) if cube is not None else None, cap, ctypes.byref(n),
+                              _stream(stream))
+        if code == -3 and not changed_only:  # TSDF_ERR_CAPACITY: retry with room for all
+            cap = int(n.value)
+            continue
+        _check(code, "map_mesh")
+        t = int(n.value)
+        return pos[:t], (keys[:t] if keys is not None else None), (cube[:t] if cube is not None else None)
+
+
 def map_reset(m: int, stream=None):
     _check(lib().map_reset(m, _stream(stream)), "map_reset")
 
@@ -413,6 +440,10 @@ class TsdfMap:
 
     def esdf_query(self, pts, dist, stream=None):
         map_esdf_query(self.handle, pts, dist, stream)
+
+    def mesh(self, min_weight: float = 1e-4, changed_only: bool = False, with_keys: bool = True,
+             cap: int = 0, stream=None):
+        return map_mesh(self.handle, min_weight, changed_only, with_keys, cap, stream)
 
     def esdf_stats(self) -> dict:
         return map_esdf_stats(self.handle)

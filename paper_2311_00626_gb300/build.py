@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgb300tsdf.so")
-SOURCES = ["kernels.cu", "esdf.cu", "tsdf_api.cu"]
+SOURCES = ["kernels.cu", "esdf.cu", "mesh.cu", "tsdf_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kEsdfThreads)
   const uint32_t nb = n_blocks(m);
   const int t = threadIdx.x;
   for (uint32_t p = blockIdx.x; p < nb; p += gridDim.x) {
-    if (!m.dirty[p]) continue;  // same value for every thread of the CTA
+    if (!(m.dirty[p] & kDirtyEsdf)) continue;  // same value for every thread of the CTA
     bool any = false, lost = false;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kEsdfThreads)
     any = __syncthreads_or(any);   // also: every thread has read dirty[p]
     lost = __syncthreads_or(lost);
     if (t == 0) {
-      m.dirty[p] = 0;
+      m.dirty[p] &= (uint8_t)~kDirtyEsdf;
       if (any) add_update(e, e.list[0], e.cnt, p, gen);
       if (lost) e.clist[atomicAdd(e.cnt + 3, 1u)] = p;
     }
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(kEsdfThreads)
         reinterpret_cast<float2*>(m.pool)[(size_t)pool * 512 + l] = make_float2(d, w);
       }
     }
-    if (t == 0 && m.dirty) m.dirty[pool] = 1;
+    if (t == 0 && m.dirty) m.dirty[pool] = kDirtyEsdf | kDirtyMesh;
   }
 }
 

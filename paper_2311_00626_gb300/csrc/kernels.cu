@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(kIntegrateThreads)
     if (t == 0) {
       m.mask[slot] = 0u;
       if (fresh) m.vals[slot] = pool;
-      if (m.dirty && val != -1) m.dirty[pool] = 1;
+      if (m.dirty && val != -1) m.dirty[pool] = kDirtyEsdf | kDirtyMesh;
     }
   }
   __syncthreads();

@@ -58,6 +58,10 @@ struct tsdf_map {
   uint32_t esdf_gen;      // generation of the last update set / tlist built
   uint32_t* esdf_host;    // pinned copy of esdf.cnt
   int64_t esdf_iters, esdf_swept, esdf_pulled;
+  // meshing scratch, allocated by the first map_mesh
+  bool mesh_on;
+  gbt::MeshDev mesh;
+  uint32_t mesh_gen;
 };
 
 namespace {
@@ -282,6 +286,11 @@ void free_map(tsdf_map* m) {
   cudaFree(m->list1);
   cudaFree(m->ctl1);
   cudaFree(m->dev.dirty);
+  if (m->mesh_on) {
+    cudaFree(m->mesh.list);
+    cudaFree(m->mesh.stamp);
+    cudaFree(m->mesh.cnt);
+  }
   if (m->esdf_on) {
     cudaFree(m->esdf.st);
     cudaFree(m->esdf.st2);
@@ -906,6 +915,96 @@ tsdf_status map_import(tsdf_map* map, const int32_t* keys_host, const float* dis
   cudaFree(dW);
   if (!ok) return cuda_fail();
   return TSDF_OK;
+}
+
+// ------------------------------------------------------------------ mesh
+
+namespace {
+
+// Marching-cubes case table.  Each face's corners are listed counter-
+// clockwise as seen from outside the cube; walking round a face, a segment
+// runs from the edge where the walk enters a run of inside corners to the
+// edge where it leaves the run (so a face with two diagonal inside corners
+// gets one segment around each).  The segments of the six faces chain into
+// loops; a loop starts at its smallest edge number and is cut into the fan
+// (e0, ei, ei+1).  Corner c = x + 2 y + 4 z; edge number 4 * axis + u + 2 w,
+// u and w the edge's coordinates on the other two axes in increasing order.
+gbt::MeshTable make_mesh_table() {
+  static const int kFaces[6][4] = {{0, 4, 6, 2}, {1, 3, 7, 5}, {0, 1, 5, 4},
+                                   {2, 6, 7, 3}, {0, 2, 3, 1}, {4, 5, 7, 6}};
+  auto edge_between = [](int a, int b) {
+    const int axis = (a ^ b) == 1 ? 0 : ((a ^ b) == 2 ? 1 : 2);
+    const int o1 = axis == 0 ? 1 : 0, o2 = axis == 2 ? 1 : 2;
+    return 4 * axis + ((a >> o1) & 1) + 2 * ((a >> o2) & 1);
+  };
+  gbt::MeshTable t;
+  std::memset(&t, 0, sizeof(t));
+  for (int ci = 0; ci < 256; ++ci) {
+    int next[12];
+    std::fill(next, next + 12, -1);
+    for (const auto& f : kFaces) {
+      for (int j = 0; j < 4; ++j) {
+        const bool out_j = !((ci >> f[j]) & 1), in_j1 = (ci >> f[(j + 1) & 3]) & 1;
+        if (!(out_j && in_j1)) continue;
+        int k = (j + 1) & 3;  // last inside corner of the run
+        while ((ci >> f[(k + 1) & 3]) & 1) k = (k + 1) & 3;
+        next[edge_between(f[j], f[(j + 1) & 3])] = edge_between(f[k], f[(k + 1) & 3]);
+      }
+    }
+    bool used[12] = {false};
+    int n = 0;
+    for (int s0 = 0; s0 < 12; ++s0) {
+      if (next[s0] < 0 || used[s0]) continue;
+      int loop[12], len = 0;
+      for (int e = s0; !used[e]; e = next[e]) {
+        used[e] = true;
+        loop[len++] = e;
+      }
+      for (int i = 1; i + 1 < len && n < 5; ++i, ++n) {
+        t.edges[ci][3 * n] = (int8_t)loop[0];
+        t.edges[ci][3 * n + 1] = (int8_t)loop[i];
+        t.edges[ci][3 * n + 2] = (int8_t)loop[i + 1];
+      }
+    }
+    t.count[ci] = (uint8_t)n;
+  }
+  return t;
+}
+
+const gbt::MeshTable& mesh_table() {
+  static const gbt::MeshTable t = make_mesh_table();
+  return t;
+}
+
+}  // namespace
+
+tsdf_status map_mesh(tsdf_map* map, float min_weight, int32_t changed_only, float* tri_pos_dev,
+                     int32_t* tri_keys_dev, int32_t* tri_cube_dev, int64_t cap, int64_t* n_tris,
+                     void* cuda_stream) {
+  if (!map || !n_tris || cap < 0 || (cap > 0 && !tri_pos_dev) || !std::isfinite(min_weight)) return TSDF_ERR_ARG;
+  if (map->storage != TSDF_STORAGE_FP32 && map->storage != TSDF_STORAGE_FP16) return TSDF_ERR_ARG;
+  if (!on_device(map)) return TSDF_ERR_STATE;
+  gbt::MeshDev& md = map->mesh;
+  if (!map->mesh_on) {
+    std::memset(&md, 0, sizeof(md));
+    map->mesh_on = true;  // free_map releases whatever was allocated
+    if (cudaMalloc(&md.list, sizeof(uint32_t) * map->max_blocks) != cudaSuccess ||
+        cudaMalloc(&md.stamp, sizeof(uint32_t) * map->max_blocks) != cudaSuccess ||
+        cudaMalloc(&md.cnt, sizeof(unsigned long long) * 2) != cudaSuccess ||
+        cudaMemset(md.stamp, 0, sizeof(uint32_t) * map->max_blocks) != cudaSuccess)
+      return cuda_fail();
+    map->mesh_gen = 0;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  unsigned long long cnt[2] = {0, 0};
+  if (cudaMemsetAsync(md.cnt, 0, sizeof(cnt), s) != cudaSuccess ||
+      gbt::launch_mesh(map->dev, md, mesh_table(), changed_only ? 1 : 0, ++map->mesh_gen, min_weight,
+                       tri_pos_dev, tri_keys_dev, tri_cube_dev, cap, s) != cudaSuccess ||
+      cudaMemcpyAsync(cnt, md.cnt, sizeof(cnt), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return cuda_fail();
+  *n_tris = (int64_t)cnt[1];
+  return cnt[1] > (unsigned long long)cap ? TSDF_ERR_CAPACITY : TSDF_OK;
 }
 
 tsdf_status map_reset(tsdf_map* map, void* cuda_stream) {

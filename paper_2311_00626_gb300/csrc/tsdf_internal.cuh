@@ -74,9 +74,10 @@ struct MapDev {
   float l_occ, l_free;            // occupancy layer: log-odds added per update
   int32_t weighting;              // TSDF weight: bit 0 inverse square depth, bit 1 drop-off
   float dropoff;                  // drop-off start behind the surface (m)
-  uint8_t* dirty;                 // [max_blocks] 1 = changed since the last ESDF update
-                                  // (may be null: no tracking)
+  uint8_t* dirty;                 // [max_blocks] kDirtyEsdf / kDirtyMesh: changed since the
+                                  // last ESDF update / mesh extraction (may be null)
 };
+enum : uint8_t { kDirtyEsdf = 1, kDirtyMesh = 2 };
 
 // ESDF layer of a map (Sec. IV-C), indexed like the pool.  State word per
 // voxel: parent offset x, y, z as 9-bit two's complement in bits 0-8, 9-17,
@@ -179,6 +180,21 @@ cudaError_t launch_esdf_query(const MapDev& m, const EsdfDev& e, const float* pt
                               float* dist, cudaStream_t s);
 cudaError_t launch_import(const MapDev& m, const int32_t* keys, const float* D, const float* W,
                           int64_t n, cudaStream_t s);
+
+// Marching-cubes case table: triangles (edge numbers) of each inside mask.
+struct MeshTable {
+  uint8_t count[256];
+  int8_t edges[256][15];
+};
+// Meshing scratch of a map, allocated by the first extraction.
+struct MeshDev {
+  uint32_t* list;     // [max_blocks] blocks to mesh
+  uint32_t* stamp;    // [max_blocks] generation that listed the block
+  unsigned long long* cnt;  // [0] list size, [1] triangles produced
+};
+cudaError_t launch_mesh(const MapDev& m, const MeshDev& md, const MeshTable& table, int changed_only,
+                        uint32_t gen, float min_weight, float* pos, int32_t* keys, int32_t* cubes,
+                        int64_t cap, cudaStream_t s);
 int integrate_ctas_per_sm(int storage);
 
 }  // namespace gbt
