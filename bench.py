@@ -433,6 +433,19 @@ def main():
         forms["esdf"] = {"blocks": m5.stats()["blocks"], "site_eps_m": v32, "max_dist_vox": 64,
                          "full_ms": full_ms, "full": full_stats,
                          "incremental_after_10_frames_ms": inc_ms, "incremental": inc_stats}
+        # marching-cubes mesh of the same map: every block, then the blocks
+        # changed by 10 more frames (and those whose cubes reach into them)
+        mesh_full = [0]
+        full_mesh_ms = esdf_ms(lambda: mesh_full.__setitem__(0, len(m5.mesh(with_keys=False, cap=1 << 22)[0])))
+        m5.mesh(changed_only=True, with_keys=False, cap=1 << 22)  # consume the changes so far
+        gt.integrate_batch([m5.handle], descs5)
+        mesh_inc = [0]
+        inc_mesh_ms = esdf_ms(lambda: mesh_inc.__setitem__(
+            0, len(m5.mesh(changed_only=True, with_keys=False, cap=1 << 22)[0])))
+        forms["mesh"] = {"full_ms": full_mesh_ms, "full_triangles": mesh_full[0],
+                         "incremental_after_10_frames_ms": inc_mesh_ms,
+                         "incremental_triangles": mesh_inc[0],
+                         "note": "includes the output allocation and the count read-back"}
         m5.close()
         forms["fp32_batched_speedup_vs_one_frame"] = ms1 / ms
         forms["fp16_batched_speedup_vs_one_frame"] = ms1 / ms2
