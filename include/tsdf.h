@@ -324,7 +324,7 @@ typedef struct {
  * max_dist.  The first call allocates the layer (8 KiB per pool block) and
  * fixes the parameters; later calls must pass the same ones.  TSDF maps
  * only (FP32 or FP16 storage).  Enqueued on cuda_stream; waits for the
- * stream once per iteration to test for convergence.
+ * stream after every four iterations to test for convergence.
  */
 tsdf_status map_esdf_update(tsdf_map* map, const tsdf_esdf_opts* opts, void* cuda_stream);
 

@@ -11,7 +11,8 @@
 //                      a site disappeared
 //   esdf_clear_kernel  in every block near one of the latter, drop parents
 //                      that are no longer sites
-//   then, until the update set is empty (the host loops):
+//   then, until the update set is empty (the host enqueues four iterations
+//   at a time and reads the set size after them):
 //   esdf_sweep_kernel  six in-block sweeps (+x, -x, +y, -y, +z, -z) of every
 //                      block of the update set, in shared memory
 //   esdf_tlist_kernel  the update set and its existing face neighbours
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(kEsdfThreads)
     }
     if (__syncthreads_or(any) && t == 0) add_update(e, e.list[0], e.cnt, p, gen);
   }
-  if (my_cleared) atomicAdd(e.cleared, my_cleared);
+  if (my_cleared) atomicAdd(e.stats, my_cleared);
 }
 
 // ------------------------------------------------------------ lower ESDF
@@ -199,10 +200,20 @@ __global__ void __launch_bounds__(kEsdfThreads)
 // Six in-block sweeps of every block of the current update set.  64 threads
 // sweep the 64 lines of an axis direction, one line each.
 __global__ void __launch_bounds__(64)
-    esdf_sweep_kernel(const EsdfDev e, const uint32_t* __restrict__ list, const uint32_t* size) {
+    esdf_sweep_kernel(const EsdfDev e, const uint32_t* __restrict__ list, const uint32_t* size,
+                      uint32_t* zero_next) {
   __shared__ uint32_t s[512];
   const uint32_t n = __ldcg(size);
   const int t = threadIdx.x;
+  if (blockIdx.x == 0 && t == 0) {
+    // sizes this iteration fills: the exchange set and the next update set
+    e.cnt[2] = 0u;
+    *zero_next = 0u;
+    if (n) {
+      atomicAdd(e.stats + 1, 1ull);
+      atomicAdd(e.stats + 2, (unsigned long long)n);
+    }
+  }
   const int max2 = e.max_dist * e.max_dist;
   for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
     const uint32_t p = list[k];
@@ -262,6 +273,7 @@ __global__ void __launch_bounds__(kEsdfThreads) esdf_pull_kernel(const MapDev m,
   const uint32_t n = __ldcg(e.cnt + 2);
   const int t = threadIdx.x;
   const int max2 = e.max_dist * e.max_dist;
+  if (blockIdx.x == 0 && t == 0 && n) atomicAdd(e.stats + 3, (unsigned long long)n);
   for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
     const uint32_t p = e.tlist[k];
     __syncthreads();
@@ -418,13 +430,14 @@ cudaError_t launch_esdf_clear(const MapDev& m, const EsdfDev& e, uint32_t gen, c
   return cudaGetLastError();
 }
 
-// One lowering iteration: sweep the current set, build tlist, exchange
-// faces, apply.  The caller zeroes the tlist and next-set sizes first.
+// One lowering iteration: sweep the current set (its first thread zeroes the
+// tlist and next-set sizes), build tlist, exchange faces, apply.  With an
+// empty current set every kernel returns at once.
 cudaError_t launch_esdf_iteration(const MapDev& m, const EsdfDev& e, int cur, uint32_t gen_t,
                                   uint32_t gen_next, cudaStream_t s) {
   uint32_t* list = cur ? e.list[1] : e.list[0];
   uint32_t* next = cur ? e.list[0] : e.list[1];
-  esdf_sweep_kernel<<<grid_for(16), 64, 0, s>>>(e, list, e.cnt + cur);
+  esdf_sweep_kernel<<<grid_for(16), 64, 0, s>>>(e, list, e.cnt + cur, e.cnt + (1 - cur));
   esdf_tlist_kernel<<<grid_for(2), 256, 0, s>>>(m, e, list, e.cnt + cur, gen_t);
   esdf_pull_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(m, e);
   esdf_apply_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(e, next, e.cnt + (1 - cur), gen_next);

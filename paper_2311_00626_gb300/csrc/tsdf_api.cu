@@ -57,7 +57,6 @@ struct tsdf_map {
   tsdf_esdf_opts esdf_opts;
   uint32_t esdf_gen;      // generation of the last update set / tlist built
   uint32_t* esdf_host;    // pinned copy of esdf.cnt
-  int64_t esdf_iters, esdf_swept, esdf_pulled;
   // meshing scratch, allocated by the first map_mesh
   bool mesh_on;
   gbt::MeshDev mesh;
@@ -302,7 +301,7 @@ void free_map(tsdf_map* m) {
     cudaFree(m->esdf.stamp_t);
     cudaFree(m->esdf.tchanged);
     cudaFree(m->esdf.cnt);
-    cudaFree(m->esdf.cleared);
+    cudaFree(m->esdf.stats);
     cudaFreeHost(m->esdf_host);
   }
   if (m->aux) cudaStreamDestroy(m->aux);
@@ -743,14 +742,14 @@ tsdf_status esdf_alloc(tsdf_map* m, const tsdf_esdf_opts& o) {
             cudaMalloc(&e.stamp_t, sizeof(uint32_t) * nb) == cudaSuccess &&
             cudaMalloc(&e.tchanged, nb) == cudaSuccess &&
             cudaMalloc(&e.cnt, sizeof(uint32_t) * 4) == cudaSuccess &&
-            cudaMalloc(&e.cleared, sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc(&e.stats, sizeof(unsigned long long) * 4) == cudaSuccess &&
             cudaMallocHost(&m->esdf_host, sizeof(uint32_t) * 4) == cudaSuccess;
   if (ok)
     ok = cudaMemset(e.st, 0, sizeof(uint32_t) * 512 * nb) == cudaSuccess &&
          cudaMemset(e.stamp_s, 0, sizeof(uint32_t) * nb) == cudaSuccess &&
          cudaMemset(e.stamp_t, 0, sizeof(uint32_t) * nb) == cudaSuccess &&
          cudaMemset(e.cnt, 0, sizeof(uint32_t) * 4) == cudaSuccess &&
-         cudaMemset(e.cleared, 0, sizeof(unsigned long long)) == cudaSuccess &&
+         cudaMemset(e.stats, 0, sizeof(unsigned long long) * 4) == cudaSuccess &&
          cudaDeviceSynchronize() == cudaSuccess;
   m->esdf_on = true;  // free_map releases whatever was allocated
   if (!ok) return cuda_fail();
@@ -759,7 +758,6 @@ tsdf_status esdf_alloc(tsdf_map* m, const tsdf_esdf_opts& o) {
   e.max_dist = o.max_dist_vox;
   m->esdf_opts = o;
   m->esdf_gen = 0;
-  m->esdf_iters = m->esdf_swept = m->esdf_pulled = 0;
   return TSDF_OK;
 }
 
@@ -797,41 +795,34 @@ tsdf_status map_esdf_update(tsdf_map* map, const tsdf_esdf_opts* opts, void* cud
       gbt::launch_esdf_mark(map->dev, e, g, s) != cudaSuccess ||
       gbt::launch_esdf_clear(map->dev, e, g, s) != cudaSuccess)
     return cuda_fail();
-  tsdf_status st = esdf_read_counts(map, s);
-  if (st != TSDF_OK) return st;
-  // lower until no block changes
+  // lower until no block changes: four iterations per read-back of the set
+  // size (iterations on an empty set return at once)
+  constexpr int kItersPerCheck = 4;
   int cur = 0;
-  uint32_t n = map->esdf_host[0];
-  while (n > 0) {
-    map->esdf_iters += 1;
-    map->esdf_swept += n;
-    const uint32_t gen_t = ++map->esdf_gen, gen_next = ++map->esdf_gen;
-    if (cudaMemsetAsync(e.cnt + 2, 0, sizeof(uint32_t), s) != cudaSuccess ||
-        cudaMemsetAsync(e.cnt + (1 - cur), 0, sizeof(uint32_t), s) != cudaSuccess ||
-        gbt::launch_esdf_iteration(map->dev, e, cur, gen_t, gen_next, s) != cudaSuccess)
-      return cuda_fail();
-    st = esdf_read_counts(map, s);
+  for (;;) {
+    for (int k = 0; k < kItersPerCheck; ++k) {
+      const uint32_t gen_t = ++map->esdf_gen, gen_next = ++map->esdf_gen;
+      if (gbt::launch_esdf_iteration(map->dev, e, cur, gen_t, gen_next, s) != cudaSuccess)
+        return cuda_fail();
+      cur = 1 - cur;
+    }
+    tsdf_status st = esdf_read_counts(map, s);
     if (st != TSDF_OK) return st;
-    map->esdf_pulled += map->esdf_host[2];
-    cur = 1 - cur;
-    n = map->esdf_host[cur];
+    if (map->esdf_host[cur] == 0) break;
   }
-  // the next update starts from set 0
-  if (cur == 1 && cudaMemsetAsync(e.cnt + 1, 0, sizeof(uint32_t), s) != cudaSuccess) return cuda_fail();
   return TSDF_OK;
 }
 
 tsdf_status map_esdf_stats(const tsdf_map* map, int64_t out[4]) {
   if (!map || !out) return TSDF_ERR_ARG;
-  unsigned long long cleared = 0;
+  unsigned long long st[4] = {0, 0, 0, 0};
   if (map->esdf_on && (cudaDeviceSynchronize() != cudaSuccess ||
-                       cudaMemcpy(&cleared, map->esdf.cleared, sizeof(cleared), cudaMemcpyDeviceToHost) !=
-                           cudaSuccess))
+                       cudaMemcpy(st, map->esdf.stats, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess))
     return cuda_fail();
-  out[0] = map->esdf_iters;
-  out[1] = map->esdf_swept;
-  out[2] = map->esdf_pulled;
-  out[3] = (int64_t)cleared;
+  out[0] = (int64_t)st[1];
+  out[1] = (int64_t)st[2];
+  out[2] = (int64_t)st[3];
+  out[3] = (int64_t)st[0];
   return TSDF_OK;
 }
 
@@ -1018,9 +1009,8 @@ tsdf_status map_reset(tsdf_map* map, void* cuda_stream) {
     return cuda_fail();
   if (map->esdf_on &&
       (cudaMemsetAsync(map->esdf.st, 0, sizeof(uint32_t) * 512 * map->max_blocks, s) != cudaSuccess ||
-       cudaMemsetAsync(map->esdf.cleared, 0, sizeof(unsigned long long), s) != cudaSuccess))
+       cudaMemsetAsync(map->esdf.stats, 0, sizeof(unsigned long long) * 4, s) != cudaSuccess))
     return cuda_fail();
-  map->esdf_iters = map->esdf_swept = map->esdf_pulled = 0;
   map->status_seen = 0;
   map->frames = 0;
   return TSDF_OK;

@@ -95,7 +95,8 @@ struct EsdfDev {
   uint32_t* stamp_t;    // [max_blocks] generation that put the block in tlist
   uint8_t* tchanged;    // [max_blocks] per tlist entry: the exchange changed the block
   uint32_t* cnt;        // [0], [1] update set sizes, [2] tlist size, [3] clist size
-  unsigned long long* cleared;  // voxels whose parent stopped being a site
+  unsigned long long* stats;    // [0] voxels whose parent stopped being a site, [1] lowering
+                                // iterations, [2] blocks swept, [3] blocks in face exchanges
   float site_eps, min_weight;
   int32_t max_dist;     // voxels, <= 255
 };
