@@ -239,7 +239,8 @@ __global__ void __launch_bounds__(kAllocThreads)
     }
   }
   const FrameDev& F = p.fr[f];
-  const MapDev& m = p.maps[F.map];
+  // with one map its fields are constant operands, not indexed loads
+  const MapDev& m = NM == 1 ? p.maps[0] : p.maps[F.map];
   const int tiles_x = (F.width + kTileW - 1) / kTileW;
   const int tile = (int)blockIdx.x - F.blk_begin;
   const int x0 = (tile % tiles_x) * kTileW, y0 = (tile / tiles_x) * TH;
@@ -662,7 +663,7 @@ __global__ void __launch_bounds__(kIntegrateThreads)
     // the CTA), so no warp waits on another before its voxel loads
     int mi = 0;
     while (mi + 1 < p.n_maps && e >= s_begin[mi + 1]) ++mi;
-    const MapDev& m = p.maps[mi];
+    const MapDev& m = NM == 1 ? p.maps[0] : p.maps[mi];
     const uint32_t slot = m.list[e - s_begin[mi]];
     const int val = m.vals[slot];
     const uint32_t slot_mask = m.mask[slot];
@@ -904,6 +905,9 @@ template cudaError_t launch_band_alloc<1, 1>(const BatchParams<1, 1>&, int, int,
 template cudaError_t launch_band_alloc<kMaxFrames, kMaxMaps>(const BatchParams<kMaxFrames, kMaxMaps>&,
                                                              int, int, cudaStream_t);
 template cudaError_t launch_integrate<1, 1>(const BatchParams<1, 1>&, int, cudaStream_t);
+template cudaError_t launch_band_alloc<kMaxFrames, 1>(const BatchParams<kMaxFrames, 1>&, int, int,
+                                                     cudaStream_t);
+template cudaError_t launch_integrate<kMaxFrames, 1>(const BatchParams<kMaxFrames, 1>&, int, cudaStream_t);
 template cudaError_t launch_integrate<kMaxFrames, kMaxMaps>(const BatchParams<kMaxFrames, kMaxMaps>&,
                                                             int, cudaStream_t);
 

@@ -489,6 +489,8 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
   }
   // the params block is large; keep it off the stack
   static thread_local BatchParams<gbt::kMaxFrames, gbt::kMaxMaps> p;
+  // single-map batches launch the one-map kernels (map fields become constants)
+  static thread_local BatchParams<gbt::kMaxFrames, 1> p1;
   tsdf_map* lead = maps[0];
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const int n_sub = (n + gbt::kMaxFrames - 1) / gbt::kMaxFrames;
@@ -524,13 +526,23 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
       return cuda_fail();
     cudaEvent_t* ev = timing_slot(lead);
     if (ev) cudaEventRecord(ev[0], sa);
-    if (gbt::launch_band_alloc(p, ctas, th, sa) != cudaSuccess) return cuda_fail();
+    if (n_maps == 1) {
+      p1.n_frames = p.n_frames;
+      p1.n_maps = 1;
+      p1.maps[0] = p.maps[0];
+      std::memcpy(p1.fr, p.fr, sizeof(p.fr));
+    }
+    if ((n_maps == 1 ? gbt::launch_band_alloc(p1, ctas, th, sa) : gbt::launch_band_alloc(p, ctas, th, sa)) !=
+        cudaSuccess)
+      return cuda_fail();
     if (ev) cudaEventRecord(ev[1], sa);
     if (piped && (cudaEventRecord(lead->ev_alloc[b & 3], sa) != cudaSuccess ||
                   cudaStreamWaitEvent(s, lead->ev_alloc[b & 3], 0) != cudaSuccess))
       return cuda_fail();
     if (ev) cudaEventRecord(ev[2], s);
-    if (gbt::launch_integrate(p, lead->n_ctas_integrate, s) != cudaSuccess) return cuda_fail();
+    if ((n_maps == 1 ? gbt::launch_integrate(p1, lead->n_ctas_integrate, s)
+                     : gbt::launch_integrate(p, lead->n_ctas_integrate, s)) != cudaSuccess)
+      return cuda_fail();
     if (ev) cudaEventRecord(ev[3], s);
     if (piped && cudaEventRecord(lead->ev_int[b & 3], s) != cudaSuccess) return cuda_fail();
   }
