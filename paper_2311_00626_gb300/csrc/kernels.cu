@@ -561,6 +561,48 @@ __device__ __forceinline__ void row_points(const FrameDev& F, float v, const Vox
   }
 }
 
+// A pinhole frame's projection constants, staged in shared memory once per
+// CTA: six 16-byte loads per frame in the voxel loop instead of one
+// constant-bank load per field (the frame index is not known at compile
+// time, so the fields cannot be instruction operands).
+struct __align__(16) FrameProj {
+  float4 r0, r1, r2;  // rows of R_CL, with t_loc in w
+  float4 cam;         // fu, fv, cu, cv
+  int4 anchor;        // a, width
+  float4 size;        // width, height (as floats), unused, unused
+};
+
+__device__ __forceinline__ void stage_frame(const FrameDev& F, FrameProj& S) {
+  S.r0 = make_float4(F.Rcl[0], F.Rcl[1], F.Rcl[2], F.tloc[0]);
+  S.r1 = make_float4(F.Rcl[3], F.Rcl[4], F.Rcl[5], F.tloc[1]);
+  S.r2 = make_float4(F.Rcl[6], F.Rcl[7], F.Rcl[8], F.tloc[2]);
+  S.cam = make_float4(F.fu, F.fv, F.cu, F.cv);
+  S.anchor = make_int4(F.a[0], F.a[1], F.a[2], F.width);
+  S.size = make_float4((float)F.width, (float)F.height, 0.0f, 0.0f);
+}
+
+// row_points with staged constants (same arithmetic).
+__device__ __forceinline__ void row_points_staged(const float4& r0, const float4& r1, const float4& r2,
+                                                  const int4& an, float v, const VoxelRow& r,
+                                                  float* px, float* py, float* pz) {
+  const int rx = (r.bx - an.x) * 8 + r.lx0;
+  const int ry = (r.by - an.y) * 8 + r.ly;
+  const int rz = (r.bz - an.z) * 8 + r.lz;
+  const float qy = __fmul_rn(__fadd_rn((float)ry, 0.5f), v);
+  const float qz = __fmul_rn(__fadd_rn((float)rz, 0.5f), v);
+  const float cx = __fmaf_rn(r0.y, qy, __fmaf_rn(r0.z, qz, r0.w));
+  const float cy = __fmaf_rn(r1.y, qy, __fmaf_rn(r1.z, qz, r1.w));
+  const float cz = __fmaf_rn(r2.y, qy, __fmaf_rn(r2.z, qz, r2.w));
+  const float fx = (float)rx;  // rx + i is exact in FP32 (|rx| < 2^24)
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float qx = __fmul_rn(__fadd_rn(__fadd_rn(fx, (float)i), 0.5f), v);
+    px[i] = __fmaf_rn(r0.x, qx, cx);
+    py[i] = __fmaf_rn(r1.x, qx, cy);
+    pz[i] = __fmaf_rn(r2.x, qx, cz);
+  }
+}
+
 // NQ consecutive pinhole frames of the batch: phase 1 projects every voxel
 // into every frame (Eq. 2, nearest pixel) and issues all depth loads (and
 // colour loads for a colour layer), phase 2 applies the updates in frame
@@ -568,29 +610,31 @@ __device__ __forceinline__ void row_points(const FrameDev& F, float v, const Vox
 // is invalid like a missing depth.  A colour layer updates only voxels within
 // tau of the surface on both sides.
 template <int NQ, int STORAGE, bool WEIGHTED, class P>
-__device__ __forceinline__ void fuse_pinhole(const P& p, const int (&fq)[4], const MapDev& m,
-                                             const VoxelRow& r, float* D, float* W, float* G,
-                                             float* B, unsigned long long& upd) {
+__device__ __forceinline__ void fuse_pinhole(const P& p, const FrameProj* s_fp, const int (&fq)[4],
+                                             const MapDev& m, const VoxelRow& r, float* D, float* W,
+                                             float* G, float* B, unsigned long long& upd) {
   float d[NQ][4], z[NQ][4];
   uint32_t c[NQ][4];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    const FrameDev& F = p.fr[fq[q]];
+    const FrameProj& S = s_fp[fq[q]];
+    const float4 r0 = S.r0, r1 = S.r1, r2 = S.r2, cam = S.cam, size = S.size;
+    const int4 an = S.anchor;
+    const float* depth = p.fr[fq[q]].depth;
     float px[4], py[4];
-    row_points(F, m.v, r, px, py, z[q]);
+    row_points_staged(r0, r1, r2, an, m.v, r, px, py, z[q]);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const float iz = __frcp_rn(z[q][i]);
-      const float u = __fadd_rn(__fmaf_rn(__fmul_rn(px[i], iz), F.fu, F.cu), 0.5f);
-      const float v = __fadd_rn(__fmaf_rn(__fmul_rn(py[i], iz), F.fv, F.cv), 0.5f);
-      const bool in = z[q][i] > 0.0f && u >= 0.0f && u < (float)F.width && v >= 0.0f &&
-                      v < (float)F.height;
+      const float u = __fadd_rn(__fmaf_rn(__fmul_rn(px[i], iz), cam.x, cam.z), 0.5f);
+      const float v = __fadd_rn(__fmaf_rn(__fmul_rn(py[i], iz), cam.y, cam.w), 0.5f);
+      const bool in = z[q][i] > 0.0f && u >= 0.0f && u < size.x && v >= 0.0f && v < size.y;
       if (STORAGE == kStorageColor) {
-        const int pix = in ? (int)v * F.width + (int)u : 0;
-        d[q][i] = in ? __ldg(F.depth + pix) : 0.0f;
-        c[q][i] = in ? __ldg(F.rgba + pix) : 0u;
+        const int pix = in ? (int)v * an.w + (int)u : 0;
+        d[q][i] = in ? __ldg(depth + pix) : 0.0f;
+        c[q][i] = in ? __ldg(p.fr[fq[q]].rgba + pix) : 0u;
       } else {
-        d[q][i] = in ? __ldg(F.depth + (int)v * F.width + (int)u) : 0.0f;
+        d[q][i] = in ? __ldg(depth + (int)v * an.w + (int)u) : 0.0f;
       }
     }
   }
@@ -636,8 +680,11 @@ __global__ void __launch_bounds__(kIntegrateThreads)
   __shared__ uint32_t s_begin[NM + 1];
   __shared__ unsigned long long s_upd[NM];
   __shared__ uint32_t s_next[2];
+  __shared__ FrameProj s_fp[NF];
   const int t = threadIdx.x;
   if (t < NM) s_upd[t] = 0ull;
+  for (int f = t; f < p.n_frames; f += kIntegrateThreads)
+    if (p.fr[f].kind == kSensorPinhole) stage_frame(p.fr[f], s_fp[f]);
   if (t == 0) s_next[0] = blockIdx.x;
   if (t == 0) {
     // the batch's work = the concatenation of every map's list
@@ -705,8 +752,8 @@ __global__ void __launch_bounds__(kIntegrateThreads)
           }
         }
         fq[2] = fq[3] = -1;
-        if (nq == 2) fuse_pinhole<2, STORAGE, WEIGHTED>(p, fq, m, vr, D, W, G, B, my_upd);
-        else if (nq == 1) fuse_pinhole<1, STORAGE, WEIGHTED>(p, fq, m, vr, D, W, G, B, my_upd);
+        if (nq == 2) fuse_pinhole<2, STORAGE, WEIGHTED>(p, s_fp, fq, m, vr, D, W, G, B, my_upd);
+        else if (nq == 1) fuse_pinhole<1, STORAGE, WEIGHTED>(p, s_fp, fq, m, vr, D, W, G, B, my_upd);
         else if (!PINHOLE_ONLY) {
           const int f = __ffs(bits) - 1;  // a LiDAR frame
           bits &= bits - 1u;
