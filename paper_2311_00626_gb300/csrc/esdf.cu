@@ -11,12 +11,13 @@
 //                      a site disappeared
 //   esdf_clear_kernel  in every block near one of the latter, drop parents
 //                      that are no longer sites
+//   esdf_nbr_kernel    the face-neighbour table of every block
 //   then, until the update set is empty (the host enqueues four iterations
 //   at a time and reads the set size after them):
 //   esdf_sweep_kernel  six in-block sweeps (+x, -x, +y, -y, +z, -z) of every
-//                      block of the update set, in shared memory
-//   esdf_tlist_kernel  the update set and its existing face neighbours
-//   esdf_pull_kernel   every such block tries, on its faces, the parents of
+//                      block of the update set, in shared memory; the block
+//                      and its existing face neighbours join the tlist
+//   esdf_pull_kernel   every tlist block tries, on its faces, the parents of
 //                      the adjacent voxels across the faces, reading the
 //                      states as they were before this step; results go to
 //                      st2
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(kEsdfThreads)
     if (t == 0) {
       m.dirty[p] &= (uint8_t)~kDirtyEsdf;
       if (any) add_update(e, e.list[0], e.cnt, p, gen);
-      if (lost) e.clist[atomicAdd(e.cnt + 3, 1u)] = p;
+      if (lost) e.clist[atomicAdd(e.cnt + 2, 1u)] = p;
     }
   }
 }
@@ -141,7 +142,7 @@ constexpr int kClearChunk = 512;
 __global__ void __launch_bounds__(kEsdfThreads)
     esdf_clear_kernel(const MapDev m, const EsdfDev e, uint32_t gen) {
   __shared__ int s_c[kClearChunk][3];
-  const uint32_t nc = __ldcg(e.cnt + 3);
+  const uint32_t nc = __ldcg(e.cnt + 2);
   if (nc == 0) return;
   const uint32_t nb = n_blocks(m);
   const int t = threadIdx.x;
@@ -197,17 +198,32 @@ __global__ void __launch_bounds__(kEsdfThreads)
 
 // ------------------------------------------------------------ lower ESDF
 
+// Face-neighbour table of every pool block (the block set does not change
+// during an update).
+__global__ void esdf_nbr_kernel(const MapDev m, const EsdfDev e) {
+  const uint32_t nb = n_blocks(m);
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < 6u * nb; k += gridDim.x * blockDim.x) {
+    const uint32_t p = k / 6u;
+    const int f = (int)(k - 6u * p);
+    const unsigned long long key = m.block_keys[p];
+    const int d = (f & 1) ? 1 : -1;
+    e.nbr[k] = pool_of(m, key_coord(key, 0) + (f >> 1 == 0 ? d : 0), key_coord(key, 1) + (f >> 1 == 1 ? d : 0),
+                       key_coord(key, 2) + (f >> 1 == 2 ? d : 0));
+  }
+}
+
 // Six in-block sweeps of every block of the current update set.  64 threads
-// sweep the 64 lines of an axis direction, one line each.
+// sweep the 64 lines of an axis direction, one line each.  Afterwards the
+// block and its existing face neighbours join this iteration's tlist.
+// Thread 0 of CTA 0 zeroes the next update set's size first (that set was
+// consumed by the previous iteration).
 __global__ void __launch_bounds__(64)
     esdf_sweep_kernel(const EsdfDev e, const uint32_t* __restrict__ list, const uint32_t* size,
-                      uint32_t* zero_next) {
+                      uint32_t* zero_next, uint32_t* tlist, uint32_t* tsize, uint32_t gen_t) {
   __shared__ uint32_t s[512];
   const uint32_t n = __ldcg(size);
   const int t = threadIdx.x;
   if (blockIdx.x == 0 && t == 0) {
-    // sizes this iteration fills: the exchange set and the next update set
-    e.cnt[2] = 0u;
     *zero_next = 0u;
     if (n) {
       atomicAdd(e.stats + 1, 1ull);
@@ -243,24 +259,9 @@ __global__ void __launch_bounds__(64)
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) g[t + 64 * i] = s[t + 64 * i];
-  }
-}
-
-// tlist = the current update set and its existing face neighbours.
-__global__ void esdf_tlist_kernel(const MapDev m, const EsdfDev e, const uint32_t* __restrict__ list,
-                                  const uint32_t* size, uint32_t gen_t) {
-  const uint32_t n = __ldcg(size);
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const uint32_t p = list[k];
-    const unsigned long long key = m.block_keys[p];
-    const int bx = key_coord(key, 0), by = key_coord(key, 1), bz = key_coord(key, 2);
-    if (atomicExch(e.stamp_t + p, gen_t) != gen_t) e.tlist[atomicAdd(e.cnt + 2, 1u)] = p;
-    for (int f = 0; f < 6; ++f) {
-      const int d = (f & 1) ? 1 : -1;
-      const int q = pool_of(m, bx + (f >> 1 == 0 ? d : 0), by + (f >> 1 == 1 ? d : 0),
-                            bz + (f >> 1 == 2 ? d : 0));
-      if (q >= 0 && atomicExch(e.stamp_t + q, gen_t) != gen_t)
-        e.tlist[atomicAdd(e.cnt + 2, 1u)] = (uint32_t)q;
+    if (t < 7) {
+      const int q = t == 6 ? (int)p : e.nbr[6 * (size_t)p + t];
+      if (q >= 0 && atomicExch(e.stamp_t + q, gen_t) != gen_t) tlist[atomicAdd(tsize, 1u)] = (uint32_t)q;
     }
   }
 }
@@ -268,22 +269,17 @@ __global__ void esdf_tlist_kernel(const MapDev m, const EsdfDev e, const uint32_
 // Face exchange: each voxel on a face of the block tries the parent of the
 // voxel across that face in the neighbouring block, faces in -x, +x, -y,
 // +y, -z, +z order; reads st only, writes the block to st2 if it changed.
-__global__ void __launch_bounds__(kEsdfThreads) esdf_pull_kernel(const MapDev m, const EsdfDev e) {
+__global__ void __launch_bounds__(kEsdfThreads)
+    esdf_pull_kernel(const EsdfDev e, const uint32_t* __restrict__ tlist, const uint32_t* tsize) {
   __shared__ int s_nb[6];
-  const uint32_t n = __ldcg(e.cnt + 2);
+  const uint32_t n = __ldcg(tsize);
   const int t = threadIdx.x;
   const int max2 = e.max_dist * e.max_dist;
   if (blockIdx.x == 0 && t == 0 && n) atomicAdd(e.stats + 3, (unsigned long long)n);
   for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
-    const uint32_t p = e.tlist[k];
+    const uint32_t p = tlist[k];
     __syncthreads();
-    if (t < 6) {
-      const unsigned long long key = m.block_keys[p];
-      const int d = (t & 1) ? 1 : -1;
-      s_nb[t] = pool_of(m, key_coord(key, 0) + (t >> 1 == 0 ? d : 0),
-                        key_coord(key, 1) + (t >> 1 == 1 ? d : 0),
-                        key_coord(key, 2) + (t >> 1 == 2 ? d : 0));
-    }
+    if (t < 6) s_nb[t] = e.nbr[6 * (size_t)p + t];
     __syncthreads();
     uint32_t v[4];
     bool any = false;
@@ -314,13 +310,17 @@ __global__ void __launch_bounds__(kEsdfThreads) esdf_pull_kernel(const MapDev m,
 }
 
 // Copy the changed blocks back; they form the next update set.
+// Thread 0 of CTA 0 zeroes the other tlist's size (used by the previous
+// iteration, filled by the next one).
 __global__ void __launch_bounds__(kEsdfThreads)
-    esdf_apply_kernel(const EsdfDev e, uint32_t* next, uint32_t* next_size, uint32_t gen_next) {
-  const uint32_t n = __ldcg(e.cnt + 2);
+    esdf_apply_kernel(const EsdfDev e, const uint32_t* __restrict__ tlist, const uint32_t* tsize,
+                      uint32_t* zero_tsize, uint32_t* next, uint32_t* next_size, uint32_t gen_next) {
+  const uint32_t n = __ldcg(tsize);
   const int t = threadIdx.x;
+  if (blockIdx.x == 0 && t == 0) *zero_tsize = 0u;
   for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
     if (!e.tchanged[k]) continue;
-    const uint32_t p = e.tlist[k];
+    const uint32_t p = tlist[k];
     reinterpret_cast<uint4*>(e.st + (size_t)p * 512)[t] =
         reinterpret_cast<const uint4*>(e.st2 + (size_t)p * 512)[t];
     if (t == 0) add_update(e, next, next_size, p, gen_next);
@@ -427,20 +427,24 @@ cudaError_t launch_esdf_mark(const MapDev& m, const EsdfDev& e, uint32_t gen, cu
 
 cudaError_t launch_esdf_clear(const MapDev& m, const EsdfDev& e, uint32_t gen, cudaStream_t s) {
   esdf_clear_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(m, e, gen);
+  esdf_nbr_kernel<<<grid_for(4), 256, 0, s>>>(m, e);
   return cudaGetLastError();
 }
 
-// One lowering iteration: sweep the current set (its first thread zeroes the
-// tlist and next-set sizes), build tlist, exchange faces, apply.  With an
-// empty current set every kernel returns at once.
+// One lowering iteration (update set `cur`, tlist `cur`): sweep and build
+// the tlist, exchange faces, apply.  With an empty current set every kernel
+// returns at once.
 cudaError_t launch_esdf_iteration(const MapDev& m, const EsdfDev& e, int cur, uint32_t gen_t,
                                   uint32_t gen_next, cudaStream_t s) {
   uint32_t* list = cur ? e.list[1] : e.list[0];
   uint32_t* next = cur ? e.list[0] : e.list[1];
-  esdf_sweep_kernel<<<grid_for(16), 64, 0, s>>>(e, list, e.cnt + cur, e.cnt + (1 - cur));
-  esdf_tlist_kernel<<<grid_for(2), 256, 0, s>>>(m, e, list, e.cnt + cur, gen_t);
-  esdf_pull_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(m, e);
-  esdf_apply_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(e, next, e.cnt + (1 - cur), gen_next);
+  uint32_t* tl = cur ? e.tlist[1] : e.tlist[0];
+  uint32_t* tsize = e.cnt + 3 + cur;
+  esdf_sweep_kernel<<<grid_for(16), 64, 0, s>>>(e, list, e.cnt + cur, e.cnt + (1 - cur), tl, tsize, gen_t);
+  esdf_pull_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(e, tl, tsize);
+  esdf_apply_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(e, tl, tsize, e.cnt + 3 + (1 - cur), next,
+                                                          e.cnt + (1 - cur), gen_next);
+  (void)m;
   return cudaGetLastError();
 }
 

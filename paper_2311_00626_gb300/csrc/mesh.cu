@@ -7,8 +7,9 @@
 //  mesh_kernel       one CTA per listed block: the block's 8^3 voxels and
 //                    the +x / +y / +z faces, edges and corner of its
 //                    neighbours (9^3 values) are staged in shared memory;
-//                    each thread meshes four cubes with the case table and
-//                    appends their triangles to the output
+//                    each thread meshes four cubes with the case table; the
+//                    block reserves its output with one atomic (a scan of
+//                    the threads' triangle counts)
 //
 // A cube joins voxel centres g .. g + (1, 1, 1) and belongs to the block
 // holding g; it is meshed only if its eight corners exist and are observed.
@@ -57,6 +58,8 @@ __global__ void __launch_bounds__(kMeshThreads)
   __shared__ float s_d[kSide * kSide * kSide];
   __shared__ uint8_t s_ok[kSide * kSide * kSide];
   __shared__ int s_pool[8];
+  __shared__ int s_warp[kMeshThreads / 32];
+  __shared__ unsigned long long s_base;
   const uint32_t n = (uint32_t)__ldcg(md.cnt);
   const int t = threadIdx.x;
   for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
@@ -91,28 +94,58 @@ __global__ void __launch_bounds__(kMeshThreads)
       s_ok[i] = ok ? 1 : 0;
     }
     __syncthreads();
-#pragma unroll 1
+    // case of each of this thread's four cubes (0 = nothing to mesh)
+    int cases[4];
+    int mine = 0;
+#pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int l = 4 * t + j;
       const int x = l & 7, y = (l >> 3) & 7, z = l >> 6;
       int ci = 0;
       bool all = true;
-      float dc[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int i = (x + (c & 1)) + kSide * (y + ((c >> 1) & 1)) + kSide * kSide * (z + (c >> 2));
-        dc[c] = s_d[i];
         all = all && s_ok[i];
-        if (dc[c] < 0.0f) ci |= 1 << c;
+        if (s_d[i] < 0.0f) ci |= 1 << c;
       }
-      if (!all) continue;
+      cases[j] = all ? ci : 0;
+      mine += tab.count[cases[j]];
+    }
+    // one output reservation per block: exclusive scan of the threads' counts
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((t & 31) >= o) incl += y;
+    }
+    if ((t & 31) == 31) s_warp[t >> 5] = incl;
+    __syncthreads();
+    if (t == 0) {
+      int acc = 0;
+      for (int w = 0; w < kMeshThreads / 32; ++w) {
+        const int c = s_warp[w];
+        s_warp[w] = acc;
+        acc += c;
+      }
+      s_base = acc ? atomicAdd(md.cnt + 1, (unsigned long long)acc) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long o = s_base + (unsigned long long)(s_warp[t >> 5] + incl - mine);
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+      const int ci = cases[j];
       const int nt = tab.count[ci];
       if (nt == 0) continue;
-      const unsigned long long base = atomicAdd(md.cnt + 1, (unsigned long long)nt);
+      const int l = 4 * t + j;
+      const int x = l & 7, y = (l >> 3) & 7, z = l >> 6;
+      float dc[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        dc[c] = s_d[(x + (c & 1)) + kSide * (y + ((c >> 1) & 1)) + kSide * kSide * (z + (c >> 2))];
       const int gx = 8 * bx + x, gy = 8 * by + y, gz = 8 * bz + z;
-      for (int tr = 0; tr < nt; ++tr) {
-        const unsigned long long o = base + tr;
-        if (o >= (unsigned long long)cap) break;
+      for (int tr = 0; tr < nt; ++tr, ++o) {
+        if (o >= (unsigned long long)cap) continue;
         if (out_cube) {
           out_cube[3 * o] = gx;
           out_cube[3 * o + 1] = gy;

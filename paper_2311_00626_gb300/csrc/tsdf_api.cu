@@ -295,7 +295,9 @@ void free_map(tsdf_map* m) {
     cudaFree(m->esdf.st2);
     cudaFree(m->esdf.list[0]);
     cudaFree(m->esdf.list[1]);
-    cudaFree(m->esdf.tlist);
+    cudaFree(m->esdf.tlist[0]);
+    cudaFree(m->esdf.tlist[1]);
+    cudaFree(m->esdf.nbr);
     cudaFree(m->esdf.clist);
     cudaFree(m->esdf.stamp_s);
     cudaFree(m->esdf.stamp_t);
@@ -748,19 +750,21 @@ tsdf_status esdf_alloc(tsdf_map* m, const tsdf_esdf_opts& o) {
             cudaMalloc(&e.st2, sizeof(uint32_t) * 512 * nb) == cudaSuccess &&
             cudaMalloc(&e.list[0], sizeof(uint32_t) * nb) == cudaSuccess &&
             cudaMalloc(&e.list[1], sizeof(uint32_t) * nb) == cudaSuccess &&
-            cudaMalloc(&e.tlist, sizeof(uint32_t) * nb) == cudaSuccess &&
+            cudaMalloc(&e.tlist[0], sizeof(uint32_t) * nb) == cudaSuccess &&
+            cudaMalloc(&e.tlist[1], sizeof(uint32_t) * nb) == cudaSuccess &&
+            cudaMalloc(&e.nbr, sizeof(int32_t) * 6 * nb) == cudaSuccess &&
             cudaMalloc(&e.clist, sizeof(uint32_t) * nb) == cudaSuccess &&
             cudaMalloc(&e.stamp_s, sizeof(uint32_t) * nb) == cudaSuccess &&
             cudaMalloc(&e.stamp_t, sizeof(uint32_t) * nb) == cudaSuccess &&
             cudaMalloc(&e.tchanged, nb) == cudaSuccess &&
-            cudaMalloc(&e.cnt, sizeof(uint32_t) * 4) == cudaSuccess &&
+            cudaMalloc(&e.cnt, sizeof(uint32_t) * 8) == cudaSuccess &&
             cudaMalloc(&e.stats, sizeof(unsigned long long) * 4) == cudaSuccess &&
-            cudaMallocHost(&m->esdf_host, sizeof(uint32_t) * 4) == cudaSuccess;
+            cudaMallocHost(&m->esdf_host, sizeof(uint32_t) * 8) == cudaSuccess;
   if (ok)
     ok = cudaMemset(e.st, 0, sizeof(uint32_t) * 512 * nb) == cudaSuccess &&
          cudaMemset(e.stamp_s, 0, sizeof(uint32_t) * nb) == cudaSuccess &&
          cudaMemset(e.stamp_t, 0, sizeof(uint32_t) * nb) == cudaSuccess &&
-         cudaMemset(e.cnt, 0, sizeof(uint32_t) * 4) == cudaSuccess &&
+         cudaMemset(e.cnt, 0, sizeof(uint32_t) * 8) == cudaSuccess &&
          cudaMemset(e.stats, 0, sizeof(unsigned long long) * 4) == cudaSuccess &&
          cudaDeviceSynchronize() == cudaSuccess;
   m->esdf_on = true;  // free_map releases whatever was allocated
@@ -774,7 +778,7 @@ tsdf_status esdf_alloc(tsdf_map* m, const tsdf_esdf_opts& o) {
 }
 
 tsdf_status esdf_read_counts(tsdf_map* m, cudaStream_t s) {
-  if (cudaMemcpyAsync(m->esdf_host, m->esdf.cnt, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost, s) !=
+  if (cudaMemcpyAsync(m->esdf_host, m->esdf.cnt, sizeof(uint32_t) * 8, cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return cuda_fail();
@@ -803,7 +807,7 @@ tsdf_status map_esdf_update(tsdf_map* map, const tsdf_esdf_opts* opts, void* cud
   EsdfDev& e = map->esdf;
   // mark sites and clear invalid parents: update set 0 gets generation g
   const uint32_t g = ++map->esdf_gen;
-  if (cudaMemsetAsync(e.cnt, 0, sizeof(uint32_t) * 4, s) != cudaSuccess ||
+  if (cudaMemsetAsync(e.cnt, 0, sizeof(uint32_t) * 8, s) != cudaSuccess ||
       gbt::launch_esdf_mark(map->dev, e, g, s) != cudaSuccess ||
       gbt::launch_esdf_clear(map->dev, e, g, s) != cudaSuccess)
     return cuda_fail();

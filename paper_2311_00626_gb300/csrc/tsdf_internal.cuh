@@ -89,12 +89,15 @@ struct EsdfDev {
   uint32_t* st;         // [max_blocks][512] voxel states
   uint32_t* st2;        // [max_blocks][512] states produced by a face exchange
   uint32_t* list[2];    // [max_blocks] update sets (current, next)
-  uint32_t* tlist;      // [max_blocks] update set and its face neighbours
+  uint32_t* tlist[2];   // [max_blocks] update set and its face neighbours (alternate
+                        // iterations use alternate lists)
   uint32_t* clist;      // [max_blocks] blocks where a site disappeared
   uint32_t* stamp_s;    // [max_blocks] generation that put the block in an update set
-  uint32_t* stamp_t;    // [max_blocks] generation that put the block in tlist
+  uint32_t* stamp_t;    // [max_blocks] generation that put the block in a tlist
   uint8_t* tchanged;    // [max_blocks] per tlist entry: the exchange changed the block
-  uint32_t* cnt;        // [0], [1] update set sizes, [2] tlist size, [3] clist size
+  int32_t* nbr;         // [max_blocks][6] pool index of each face neighbour (-x, +x, -y,
+                        // +y, -z, +z), -1 if none; rebuilt by every update
+  uint32_t* cnt;        // [0], [1] update set sizes, [2] clist size, [3], [4] tlist sizes
   unsigned long long* stats;    // [0] voxels whose parent stopped being a site, [1] lowering
                                 // iterations, [2] blocks swept, [3] blocks in face exchanges
   float site_eps, min_weight;
