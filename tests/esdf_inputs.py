@@ -24,7 +24,7 @@ def tsdf_region(lo, hi, sdf, tau=4 * 0.05, observed=None):
     return keys, D, W, g
 
 
-def brute_edt2(g, site_mask, obs_mask, chunk=4096):
+def brute_edt2(g, site_mask, obs_mask, chunk=512):
     """Exact squared distance (voxels) from every voxel to the nearest site."""
     sites = g[site_mask].astype(np.int64)
     pts = g.reshape(-1, 3).astype(np.int64)
