@@ -204,6 +204,20 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
                             int32_t n, void* cuda_stream);
 
 /*
+ * integrate_batch_host — integrate_batch for images in HOST memory: each
+ * frame's depth_dev (and color_dev) points to host memory, pinned for the
+ * copies to overlap the GPU work.  The images of sub-batch b are copied into
+ * half b % 2 of staging_dev (a caller-owned device buffer, 256-byte aligned)
+ * on an internal copy stream of the first map while the previous sub-batch
+ * integrates; contiguous host images of a sub-batch are copied at once.
+ * staging_bytes must hold two sub-batches' images (each image rounded up to
+ * 256 bytes); TSDF_ERR_ARG otherwise.  Same result as integrate_batch.  The
+ * host images must stay valid until the stream passes the call.
+ */
+tsdf_status integrate_batch_host(tsdf_map* const* maps, int32_t n_maps, const tsdf_frame_desc* frames,
+                                 int32_t n, void* staging_dev, int64_t staging_bytes, void* cuda_stream);
+
+/*
  * query_voxels — TSDF value at n points (float32 [n][3], layer frame,
  * metres): the voxel containing each point, looked up in the block hash.
  * Writes dist_dev[n] and weight_dev[n]; unallocated or unobserved voxels

@@ -25,7 +25,7 @@ __all__ = ["TsdfError", "Pinhole", "Lidar", "MapOpts", "FrameDesc", "TsdfMap", "
            "LAYER_OCCUPANCY", "LAYER_COLOR", "STORAGE_FP32", "STORAGE_FP16",
            "integrate_color", "query_color", "map_export_color", "map_decay_occupancy",
            "EsdfOpts", "map_import", "map_esdf_update", "map_esdf_export", "map_esdf_query",
-           "map_esdf_stats", "map_walk_stats", "map_mesh",
+           "map_esdf_stats", "map_walk_stats", "map_mesh", "integrate_batch_host", "frame_desc_host",
            "SENSOR_PINHOLE", "SENSOR_LIDAR", "EXPORTED_SYMBOLS"]
 
 STORAGE_FP32, STORAGE_FP16 = 0, 1
@@ -41,7 +41,7 @@ EXPORTED_SYMBOLS = ["map_create", "map_create_ex", "integrate_depth", "integrate
                     "integrate_depth_static", "integrate_color", "query_color",
                     "map_export_color", "map_decay_occupancy", "map_import", "map_esdf_update",
                     "map_esdf_export", "map_esdf_query", "map_esdf_stats", "map_walk_stats",
-                    "map_mesh"]
+                    "map_mesh", "integrate_batch_host"]
 
 
 class TsdfError(RuntimeError):
@@ -111,6 +111,7 @@ def lib():
                 "integrate_depth": ([P, P, ctypes.POINTER(Pinhole), P, P], I),
                 "integrate_lidar": ([P, P, ctypes.POINTER(Lidar), P, P], I),
                 "integrate_batch": ([P, I, ctypes.POINTER(FrameDesc), I, P], I),
+                "integrate_batch_host": ([P, I, ctypes.POINTER(FrameDesc), I, P, L64, P], I),
                 "query_voxels": ([P, P, L64, P, P, P], I),
                 "map_sync": ([P], I),
                 "map_num_blocks": ([P, ctypes.POINTER(ctypes.c_int64)], I),
@@ -222,6 +223,17 @@ def integrate_batch(maps, frames, stream=None):
     arr_f = (FrameDesc * len(frames))(*frames)
     _check(lib().integrate_batch(arr_m, len(maps), arr_f, len(frames), _stream(stream)),
            "integrate_batch")
+
+
+def integrate_batch_host(maps, frames, staging, stream=None):
+    """frames: FrameDesc with host image pointers (frame_desc_host);
+    staging: a CUDA uint8 (or any) tensor of at least two sub-batches' image
+    bytes, 256-byte aligned."""
+    arr_m = (ctypes.c_void_p * len(maps))(*maps)
+    arr_f = (FrameDesc * len(frames))(*frames)
+    nbytes = staging.numel() * staging.element_size()
+    _check(lib().integrate_batch_host(arr_m, len(maps), arr_f, len(frames), staging.data_ptr(), nbytes,
+                                      _stream(stream)), "integrate_batch_host")
 
 
 def query_voxels(m: int, pts, dist, weight, stream=None):
@@ -464,6 +476,17 @@ class TsdfMap:
             self.close()
         except Exception:
             pass
+
+
+def frame_desc_host(map_index: int, sensor: dict, T, depth, rgba=None) -> FrameDesc:
+    """As frame_desc with host images (contiguous CPU tensors, pinned for
+    overlapped copies) for integrate_batch_host."""
+    for t in (depth, rgba):
+        if t is not None and (t.is_cuda or not t.is_contiguous()):
+            raise ValueError("expected a contiguous host tensor")
+    fd = frame_desc(map_index, sensor, T, depth.data_ptr())
+    fd.color_dev = rgba.data_ptr() if rgba is not None else None
+    return fd
 
 
 def frame_desc(map_index: int, sensor: dict, T, depth, rgba=None) -> FrameDesc:

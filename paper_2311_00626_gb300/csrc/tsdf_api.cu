@@ -47,6 +47,9 @@ struct tsdf_map {
   unsigned int* ctl1;
   cudaStream_t aux;
   cudaEvent_t ev_alloc[4], ev_int[4], ev_start;
+  // host-input batches: copy stream and per-sub-batch copy events (lazy)
+  cudaStream_t copy;
+  cudaEvent_t ev_copy[4];
   // diagnostics: per call (alloc start, alloc end, integrate start, integrate end)
   bool timing;
   std::vector<cudaEvent_t> events;
@@ -307,6 +310,9 @@ void free_map(tsdf_map* m) {
     cudaFreeHost(m->esdf_host);
   }
   if (m->aux) cudaStreamDestroy(m->aux);
+  if (m->copy) cudaStreamDestroy(m->copy);
+  for (int i = 0; i < 4; ++i)
+    if (m->ev_copy[i]) cudaEventDestroy(m->ev_copy[i]);
   for (int i = 0; i < 4; ++i) {
     if (m->ev_alloc[i]) cudaEventDestroy(m->ev_alloc[i]);
     if (m->ev_int[i]) cudaEventDestroy(m->ev_int[i]);
@@ -467,8 +473,14 @@ tsdf_status integrate_lidar(tsdf_map* map, const float* range_dev, const tsdf_li
                        cuda_stream);
 }
 
-tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_frame_desc* frames,
-                            int32_t n, void* cuda_stream) {
+}  // extern "C"
+
+namespace {
+
+// Checks the maps and frames of a batch and prepares every frame (FP32 pose
+// constants, sensor tables) before anything is enqueued.
+tsdf_status prepare_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_frame_desc* frames, int32_t n,
+                          std::vector<FrameDev>& fr) {
   if (!maps || !frames || n_maps <= 0 || n_maps > gbt::kMaxMaps || n <= 0 || n > kMaxBatchFrames)
     return TSDF_ERR_ARG;
   for (int i = 0; i < n_maps; ++i) {
@@ -479,8 +491,6 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
     if (!on_device(maps[i])) return TSDF_ERR_STATE;
     if (status_from_bits(maps[i]->status_seen) != TSDF_OK) return status_from_bits(maps[i]->status_seen);
   }
-  // every frame is checked and prepared before anything is enqueued
-  static thread_local std::vector<FrameDev> fr;
   fr.resize(n);
   for (int f = 0; f < n; ++f) {
     const tsdf_frame_desc& fd = frames[f];
@@ -489,24 +499,40 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
                                 fd.depth_dev, fd.color_dev, fd.T_world_sensor, fr[f]);
     if (st != TSDF_OK) return st;
   }
+  return TSDF_OK;
+}
+
+// Called before sub-batch b (frames f0 .. f0 + nf - 1) is filled in and its
+// allocation is enqueued on stream sa; may rewrite the frames' image
+// pointers and make sa wait for copies.
+using SubBatchHook = tsdf_status (*)(void* ctx, int b, int f0, int nf, cudaStream_t sa);
+
+// Sub-batches of up to 32 frames, each one allocation launch and one
+// integration launch.  With more than one, sub-batch b uses mask / list set
+// b % 2 and its allocation runs on the lead map's auxiliary stream,
+// overlapping the integration of sub-batch b - 1 on the caller's stream; it
+// waits for the integration of b - 2, which used the same set.
+tsdf_status run_batch(tsdf_map* const* maps, int32_t n_maps, std::vector<FrameDev>& fr, int32_t n,
+                      cudaStream_t s, SubBatchHook hook, void* ctx) {
   // the params block is large; keep it off the stack
   static thread_local BatchParams<gbt::kMaxFrames, gbt::kMaxMaps> p;
   // single-map batches launch the one-map kernels (map fields become constants)
   static thread_local BatchParams<gbt::kMaxFrames, 1> p1;
   tsdf_map* lead = maps[0];
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   const int n_sub = (n + gbt::kMaxFrames - 1) / gbt::kMaxFrames;
-  // Sub-batches of up to 32 frames, each one allocation launch and one
-  // integration launch.  With more than one, sub-batch b uses mask / list
-  // set b % 2 and its allocation runs on the lead map's auxiliary stream,
-  // overlapping the integration of sub-batch b - 1 on the caller's stream;
-  // it waits for the integration of b - 2, which used the same set.
   const bool piped = n_sub > 1;
   if (piped && (cudaEventRecord(lead->ev_start, s) != cudaSuccess ||
                 cudaStreamWaitEvent(lead->aux, lead->ev_start, 0) != cudaSuccess))
     return cuda_fail();
   for (int b = 0; b < n_sub; ++b) {
     const int f0 = b * gbt::kMaxFrames, nf = std::min(gbt::kMaxFrames, n - f0);
+    cudaStream_t sa = piped ? lead->aux : s;
+    if (piped && b >= 2 && cudaStreamWaitEvent(sa, lead->ev_int[(b - 2) & 3], 0) != cudaSuccess)
+      return cuda_fail();
+    if (hook) {
+      tsdf_status st = hook(ctx, b, f0, nf, sa);
+      if (st != TSDF_OK) return st;
+    }
     std::memset(&p, 0, sizeof(p));
     p.n_frames = nf;
     p.n_maps = n_maps;
@@ -523,9 +549,6 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
       p.fr[f].blk_begin = ctas;
       ctas += alloc_ctas(p.fr[f], th);
     }
-    cudaStream_t sa = piped ? lead->aux : s;
-    if (piped && b >= 2 && cudaStreamWaitEvent(sa, lead->ev_int[(b - 2) & 3], 0) != cudaSuccess)
-      return cuda_fail();
     cudaEvent_t* ev = timing_slot(lead);
     if (ev) cudaEventRecord(ev[0], sa);
     if (n_maps == 1) {
@@ -548,6 +571,115 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
     if (ev) cudaEventRecord(ev[3], s);
     if (piped && cudaEventRecord(lead->ev_int[b & 3], s) != cudaSuccess) return cuda_fail();
   }
+  return TSDF_OK;
+}
+
+// Host-input batches: the images of sub-batch b are copied from host memory
+// into half b % 2 of the caller's staging buffer on the lead map's copy
+// stream (one copy per run of frames contiguous in host memory), after the
+// integration of sub-batch b - 2, which read that half; the sub-batch's
+// allocation waits for its copies.
+struct HostStaging {
+  tsdf_map* lead;
+  std::vector<FrameDev>* fr;
+  char* base;
+  int64_t half;                  // bytes per half of the staging buffer
+  std::vector<int64_t> off;      // per frame: depth offset in its half (colour follows)
+  std::vector<int64_t> bytes;    // per frame: depth bytes
+};
+
+int64_t align256(int64_t x) { return (x + 255) / 256 * 256; }
+
+tsdf_status stage_sub_batch(void* ctx, int b, int f0, int nf, cudaStream_t sa) {
+  HostStaging& h = *static_cast<HostStaging*>(ctx);
+  tsdf_map* lead = h.lead;
+  std::vector<FrameDev>& fr = *h.fr;
+  cudaStream_t c = lead->copy;
+  if (b >= 2 && cudaStreamWaitEvent(c, lead->ev_int[(b - 2) & 3], 0) != cudaSuccess) return cuda_fail();
+  char* half = h.base + (int64_t)(b & 1) * h.half;
+  // copy runs of frames whose images are contiguous both on the host and in the half
+  int f = f0;
+  while (f < f0 + nf) {
+    const char* src = reinterpret_cast<const char*>(fr[f].depth);
+    int64_t len = h.bytes[f];
+    int g = f + 1;
+    while (g < f0 + nf && !fr[g].rgba && !fr[f].rgba &&
+           reinterpret_cast<const char*>(fr[g].depth) == src + len && h.off[g] == h.off[f] + len) {
+      len += h.bytes[g];
+      ++g;
+    }
+    if (cudaMemcpyAsync(half + h.off[f], src, (size_t)len, cudaMemcpyHostToDevice, c) != cudaSuccess)
+      return cuda_fail();
+    for (int k = f; k < g; ++k) {
+      if (fr[k].rgba &&
+          cudaMemcpyAsync(half + h.off[k] + h.bytes[k], fr[k].rgba, (size_t)h.bytes[k], cudaMemcpyHostToDevice,
+                          c) != cudaSuccess)
+        return cuda_fail();
+      fr[k].depth = reinterpret_cast<const float*>(half + h.off[k]);
+      if (fr[k].rgba) fr[k].rgba = reinterpret_cast<const uint32_t*>(half + h.off[k] + h.bytes[k]);
+    }
+    f = g;
+  }
+  if (cudaEventRecord(lead->ev_copy[b & 3], c) != cudaSuccess ||
+      cudaStreamWaitEvent(sa, lead->ev_copy[b & 3], 0) != cudaSuccess)
+    return cuda_fail();
+  return TSDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_frame_desc* frames,
+                            int32_t n, void* cuda_stream) {
+  static thread_local std::vector<FrameDev> fr;
+  tsdf_status st = prepare_batch(maps, n_maps, frames, n, fr);
+  if (st != TSDF_OK) return st;
+  st = run_batch(maps, n_maps, fr, n, (cudaStream_t)cuda_stream, nullptr, nullptr);
+  if (st != TSDF_OK) return st;
+  for (int f = 0; f < n; ++f) maps[frames[f].map]->frames += 1;
+  return TSDF_OK;
+}
+
+tsdf_status integrate_batch_host(tsdf_map* const* maps, int32_t n_maps, const tsdf_frame_desc* frames,
+                                 int32_t n, void* staging_dev, int64_t staging_bytes, void* cuda_stream) {
+  static thread_local std::vector<FrameDev> fr;
+  tsdf_status st = prepare_batch(maps, n_maps, frames, n, fr);
+  if (st != TSDF_OK) return st;
+  if (!staging_dev || staging_bytes <= 0 || (reinterpret_cast<uintptr_t>(staging_dev) & 255u)) return TSDF_ERR_ARG;
+  HostStaging h;
+  h.lead = maps[0];
+  h.fr = &fr;
+  h.base = static_cast<char*>(staging_dev);
+  h.off.resize(n);
+  h.bytes.resize(n);
+  int64_t need = 0;
+  for (int f0 = 0; f0 < n; f0 += gbt::kMaxFrames) {
+    int64_t o = 0;
+    for (int f = f0; f < std::min(n, f0 + gbt::kMaxFrames); ++f) {
+      h.bytes[f] = (int64_t)fr[f].width * fr[f].height * 4;
+      h.off[f] = o;
+      o += align256(h.bytes[f]) * (fr[f].rgba ? 2 : 1);
+    }
+    need = std::max(need, o);
+  }
+  h.half = align256(need);
+  if (2 * h.half > staging_bytes) return TSDF_ERR_ARG;  // two sub-batches must fit
+  tsdf_map* lead = maps[0];
+  if (!lead->copy) {
+    bool ok = cudaStreamCreateWithFlags(&lead->copy, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i < 4; ++i)
+      ok = cudaEventCreateWithFlags(&lead->ev_copy[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return cuda_fail();
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // the copies start after the caller's earlier work on the stream (which may
+  // still read the staging buffer)
+  if (cudaEventRecord(lead->ev_start, s) != cudaSuccess ||
+      cudaStreamWaitEvent(lead->copy, lead->ev_start, 0) != cudaSuccess)
+    return cuda_fail();
+  st = run_batch(maps, n_maps, fr, n, s, stage_sub_batch, &h);
+  if (st != TSDF_OK) return st;
   for (int f = 0; f < n; ++f) maps[frames[f].map]->frames += 1;
   return TSDF_OK;
 }
