@@ -150,3 +150,14 @@ def test_ambiguous_face_separates_inside_corners():
     tris = oracle.mesh_case(0b00001001)
     assert len(tris) == 2
     assert sorted(map(sorted, tris.tolist())) == [[0, 4, 8], [1, 5, 11]]
+
+
+def test_zero_is_outside():
+    """D = 0 counts as outside (inside is D < 0): for D = (z index - 8)
+    voxels the vertices sit on the edges from z index 7 to 8, at t = 1."""
+    keys, D, W, g = tsdf_region((0, 0, 0), (2, 2, 2), lambda c: np.zeros(c.shape[:-1]))
+    D = (g[..., 2] - 8).astype(np.float32) * np.float32(V)
+    _, k, pos = oracle.mesh_extract(keys, D, W, float(V))
+    assert len(k) > 0
+    assert np.all(k[..., 3] == 2) and np.all(k[..., 2] == 7)
+    np.testing.assert_allclose(pos[..., 2], (8 + 0.5) * float(V), rtol=0, atol=1e-12)
