@@ -250,8 +250,9 @@ tsdf_status map_num_blocks(const tsdf_map* map, int64_t* out);
  * summed over launches), out[5] integration launches, out[6] band segments
  * walked (valid pixels), out[7] block-grid cells emitted by those walks
  * (counting a block once per pixel that meets it); out[6] and out[7] count
- * only while map_walk_stats is enabled. */
-tsdf_status map_stats(const tsdf_map* map, int64_t out[8]);
+ * only while map_walk_stats is enabled; out[8] (block, frame) pairs
+ * integrated (each projects the block's 512 voxels into the frame). */
+tsdf_status map_stats(const tsdf_map* map, int64_t out[9]);
 
 /* map_walk_stats — diagnostics: while enabled, allocation launches that
  * include this map count band segments and walked block-grid cells into

@@ -259,11 +259,11 @@ def map_num_blocks(m: int) -> int:
 
 
 def map_stats(m: int) -> dict:
-    out = np.zeros(8, np.int64)
+    out = np.zeros(9, np.int64)
     _check(lib().map_stats(m, out.ctypes.data_as(ctypes.c_void_p)), "map_stats")
     return {"blocks": int(out[0]), "voxel_updates": int(out[1]), "frames": int(out[2]),
             "status_bits": int(out[3]), "block_visits": int(out[4]), "launches": int(out[5]),
-            "segments": int(out[6]), "cells": int(out[7])}
+            "segments": int(out[6]), "cells": int(out[7]), "block_frame_pairs": int(out[8])}
 
 
 def map_walk_stats(m: int, enable: bool = True):

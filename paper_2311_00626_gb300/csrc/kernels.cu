@@ -679,10 +679,11 @@ __global__ void __launch_bounds__(kIntegrateThreads)
     integrate_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
   __shared__ uint32_t s_begin[NM + 1];
   __shared__ unsigned long long s_upd[NM];
+  __shared__ unsigned long long s_pairs[NM];
   __shared__ uint32_t s_next[2];
   __shared__ FrameProj s_fp[NF];
   const int t = threadIdx.x;
-  if (t < NM) s_upd[t] = 0ull;
+  if (t < NM) s_upd[t] = s_pairs[t] = 0ull;
   for (int f = t; f < p.n_frames; f += kIntegrateThreads)
     if (p.fr[f].kind == kSensorPinhole) stage_frame(p.fr[f], s_fp[f]);
   if (t == 0) s_next[0] = blockIdx.x;
@@ -767,6 +768,7 @@ __global__ void __launch_bounds__(kIntegrateThreads)
     if ((t & 31) == 0 && my_upd) atomicAdd(&s_upd[mi], my_upd);
     __syncthreads();  // every warp has read this entry's metadata
     if (t == 0) {
+      atomicAdd(&s_pairs[mi], (unsigned long long)__popc(slot_mask));
       m.mask[slot] = 0u;
       if (fresh) m.vals[slot] = pool;
       if (m.dirty && val != -1) m.dirty[pool] = kDirtyEsdf | kDirtyMesh;
@@ -774,6 +776,7 @@ __global__ void __launch_bounds__(kIntegrateThreads)
   }
   __syncthreads();
   if (t < p.n_maps && s_upd[t]) atomicAdd(p.maps[t].counters + kCntUpdates, s_upd[t]);
+  if (t < p.n_maps && s_pairs[t]) atomicAdd(p.maps[t].counters + kCntPairs, s_pairs[t]);
   // the last CTA to finish resets every map's work list for the next batch
   if (t == 0) {
     __threadfence();

@@ -723,7 +723,7 @@ tsdf_status map_num_blocks(const tsdf_map* map, int64_t* out) {
   return TSDF_OK;
 }
 
-tsdf_status map_stats(const tsdf_map* map, int64_t out[8]) {
+tsdf_status map_stats(const tsdf_map* map, int64_t out[9]) {
   if (!map || !out) return TSDF_ERR_ARG;
   unsigned long long c[gbt::kNumCounters];
   tsdf_status st = read_counters(map, c);
@@ -736,6 +736,7 @@ tsdf_status map_stats(const tsdf_map* map, int64_t out[8]) {
   out[5] = (int64_t)c[gbt::kCntLaunches];
   out[6] = (int64_t)c[gbt::kCntSegments];
   out[7] = (int64_t)c[gbt::kCntCells];
+  out[8] = (int64_t)c[gbt::kCntPairs];
   return TSDF_OK;
 }
 

@@ -34,6 +34,7 @@ enum : int {
   kCntLaunches = 4, // integration launches
   kCntSegments = 5, // band segments walked by the allocator (valid pixels in range)
   kCntCells = 6,    // cells emitted by those walks (with repeats across pixels)
+  kCntPairs = 7,    // (block, frame) pairs integrated: 512 voxel projections each
   kNumCounters = 8
 };
 // Sticky status bits.

@@ -14,13 +14,16 @@ def run_oracle(frames, voxel_size, trunc=4, wmax=100.0, lidar_nearest=False, gua
         m.set_occupancy(*occupancy)
     if weighting:
         m.set_weighting(weighting)
-    cells = 0
+    cells = pairs = 0
     for f in frames:
         m.integrate(f.sensor, f.T, f.depth)
-        cells += m.counters()["candidates"]
+        c = m.counters()
+        cells += c["candidates"]
+        pairs += c["band_blocks"]
     out = m.export()
     counters = m.counters()
     counters["total_cells"] = cells
+    counters["total_band_blocks"] = pairs
     m.close()
     return out, counters
 

@@ -49,6 +49,7 @@ def test_room_300_frames_fp32(room):
     st = compare(gpu, orc, 1e-4 * float(np.float32(w.voxel_size)), "room300_fp32")
     assert gs["voxel_updates"] == oc["total_updates"]
     assert gs["cells"] == oc["total_cells"]
+    assert gs["block_frame_pairs"] == oc["total_band_blocks"]
     v = float(np.float32(w.voxel_size))
     _record("room300_fp32", {**st, "max_err_vox": st["max_err"] / v, "rms_err_vox": st["rms_err"] / v})
 

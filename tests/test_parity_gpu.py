@@ -57,8 +57,10 @@ def _parity(name, frames, v, tol, **kw):
     assert status == 0, f"device status {status}"
     st = compare(gpu, orc, tol, name)
     assert gs["voxel_updates"] == oc["total_updates"], (gs, oc)
-    # the allocator emitted exactly the oracle's cells (same walks)
+    # the allocator emitted exactly the oracle's cells (same walks), and every
+    # frame's band set reached the integration (one (block, frame) pair each)
     assert gs["cells"] == oc["total_cells"], (gs, oc)
+    assert gs["block_frame_pairs"] == oc["total_band_blocks"], (gs, oc)
     _record(name, st)
     return st
 
