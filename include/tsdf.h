@@ -9,7 +9,10 @@
  * (Sec. IV-B "Frame Integration", Eq. 1-3).  Sensors follow the problem
  * statement (Sec. III): a depth image D: Omega -> d with Omega the pinhole
  * image plane (z-depth) or the LiDAR beam angles (range), taken at a pose
- * T_LC in SE(3) of the sensor in the layer frame.
+ * T_LC in SE(3) of the sensor in the layer frame.  On the same block
+ * structure the library also keeps an occupancy or colour layer instead of
+ * the TSDF (TSDF_LAYER_*), and derives from a TSDF layer its incremental
+ * ESDF (Sec. IV-C, map_esdf_*) and a marching-cubes mesh (map_mesh).
  *
  * Conventions shared by every call:
  *  - All buffers are owned by the caller.  Pointers named *_dev are device
