@@ -594,12 +594,19 @@ __device__ __forceinline__ void row_points_staged(const float4& r0, const float4
   const float cy = __fmaf_rn(r1.y, qy, __fmaf_rn(r1.z, qz, r1.w));
   const float cz = __fmaf_rn(r2.y, qy, __fmaf_rn(r2.z, qz, r2.w));
   const float fx = (float)rx;  // rx + i is exact in FP32 (|rx| < 2^24)
+  // voxel pairs on the paired FP32 operations (per component the same
+  // round-to-nearest result as the scalar ones)
+  const float2 half = make_float2(0.5f, 0.5f), vv = make_float2(v, v);
+  const float2 c0 = make_float2(cx, cx), c1 = make_float2(cy, cy), c2 = make_float2(cz, cz);
+  const float2 a0 = make_float2(r0.x, r0.x), a1 = make_float2(r1.x, r1.x), a2 = make_float2(r2.x, r2.x);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float qx = __fmul_rn(__fadd_rn(__fadd_rn(fx, (float)i), 0.5f), v);
-    px[i] = __fmaf_rn(r0.x, qx, cx);
-    py[i] = __fmaf_rn(r1.x, qx, cy);
-    pz[i] = __fmaf_rn(r2.x, qx, cz);
+  for (int i = 0; i < 4; i += 2) {
+    const float2 qx = __fmul2_rn(__fadd2_rn(__fadd2_rn(make_float2(fx, fx), make_float2((float)i, (float)(i + 1))),
+                                            half), vv);
+    const float2 x = __ffma2_rn(a0, qx, c0), y = __ffma2_rn(a1, qx, c1), z = __ffma2_rn(a2, qx, c2);
+    px[i] = x.x; px[i + 1] = x.y;
+    py[i] = y.x; py[i + 1] = y.y;
+    pz[i] = z.x; pz[i + 1] = z.y;
   }
 }
 
@@ -623,11 +630,22 @@ __device__ __forceinline__ void fuse_pinhole(const P& p, const FrameProj* s_fp, 
     const float* depth = p.fr[fq[q]].depth;
     float px[4], py[4];
     row_points_staged(r0, r1, r2, an, m.v, r, px, py, z[q]);
+    // pixel coordinates of voxel pairs on the paired FP32 operations
+    float uu[4], vv[4];
+    const float2 fu2 = make_float2(cam.x, cam.x), cu2 = make_float2(cam.z, cam.z);
+    const float2 fv2 = make_float2(cam.y, cam.y), cv2 = make_float2(cam.w, cam.w);
+    const float2 half = make_float2(0.5f, 0.5f);
+#pragma unroll
+    for (int i = 0; i < 4; i += 2) {
+      const float2 iz = make_float2(__frcp_rn(z[q][i]), __frcp_rn(z[q][i + 1]));
+      const float2 u = __fadd2_rn(__ffma2_rn(__fmul2_rn(make_float2(px[i], px[i + 1]), iz), fu2, cu2), half);
+      const float2 v = __fadd2_rn(__ffma2_rn(__fmul2_rn(make_float2(py[i], py[i + 1]), iz), fv2, cv2), half);
+      uu[i] = u.x; uu[i + 1] = u.y;
+      vv[i] = v.x; vv[i + 1] = v.y;
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const float iz = __frcp_rn(z[q][i]);
-      const float u = __fadd_rn(__fmaf_rn(__fmul_rn(px[i], iz), cam.x, cam.z), 0.5f);
-      const float v = __fadd_rn(__fmaf_rn(__fmul_rn(py[i], iz), cam.y, cam.w), 0.5f);
+      const float u = uu[i], v = vv[i];
       const bool in = z[q][i] > 0.0f && u >= 0.0f && u < size.x && v >= 0.0f && v < size.y;
       if (STORAGE == kStorageColor) {
         const int pix = in ? (int)v * an.w + (int)u : 0;
