@@ -345,7 +345,7 @@ def main():
     # sub-batch's frames from pinned host memory into a staging buffer while
     # the previous sub-batch integrates
     host_descs = [gt.frame_desc_host(0, f.sensor, f.T, host[i]) for i, f in enumerate(w.frames)]
-    staging = torch.empty(2 * 32 * host[0].numel() * 4, dtype=torch.uint8, device="cuda")
+    staging = torch.empty(4 * 32 * host[0].numel() * 4, dtype=torch.uint8, device="cuda")  # 4 slots
     host_res = torch.zeros(6, dtype=torch.int64)
 
     def e2e_step():

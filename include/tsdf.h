@@ -209,13 +209,14 @@ tsdf_status integrate_batch(tsdf_map* const* maps, int32_t n_maps, const tsdf_fr
 /*
  * integrate_batch_host — integrate_batch for images in HOST memory: each
  * frame's depth_dev (and color_dev) points to host memory, pinned for the
- * copies to overlap the GPU work.  The images of sub-batch b are copied into
- * half b % 2 of staging_dev (a caller-owned device buffer, 256-byte aligned)
- * on an internal copy stream of the first map while the previous sub-batch
- * integrates; contiguous host images of a sub-batch are copied at once.
- * staging_bytes must hold two sub-batches' images (each image rounded up to
- * 256 bytes); TSDF_ERR_ARG otherwise.  Same result as integrate_batch.  The
- * host images must stay valid until the stream passes the call.
+ * copies to overlap the GPU work.  staging_dev (a caller-owned device
+ * buffer, 256-byte aligned) is cut into as many slots of one sub-batch's
+ * images (each image rounded up to 256 bytes) as fit, 2 to 4; the images of
+ * sub-batch b are copied into slot b % slots on an internal copy stream of
+ * the first map while earlier sub-batches integrate (contiguous host images
+ * of a sub-batch are copied at once).  staging_bytes must hold two slots;
+ * TSDF_ERR_ARG otherwise.  Same result as integrate_batch.  The host images
+ * must stay valid until the stream passes the call.
  */
 tsdf_status integrate_batch_host(tsdf_map* const* maps, int32_t n_maps, const tsdf_frame_desc* frames,
                                  int32_t n, void* staging_dev, int64_t staging_bytes, void* cuda_stream);

@@ -575,15 +575,17 @@ tsdf_status run_batch(tsdf_map* const* maps, int32_t n_maps, std::vector<FrameDe
 }
 
 // Host-input batches: the images of sub-batch b are copied from host memory
-// into half b % 2 of the caller's staging buffer on the lead map's copy
+// into slot b % slots of the caller's staging buffer on the lead map's copy
 // stream (one copy per run of frames contiguous in host memory), after the
-// integration of sub-batch b - 2, which read that half; the sub-batch's
-// allocation waits for its copies.
+// integration of sub-batch b - slots, which read that slot; the sub-batch's
+// allocation waits for its copies.  With more slots the copies run further
+// ahead of the kernels.
 struct HostStaging {
   tsdf_map* lead;
   std::vector<FrameDev>* fr;
   char* base;
-  int64_t half;                  // bytes per half of the staging buffer
+  int64_t half;                  // bytes per slot of the staging buffer
+  int slots;                     // 2 .. 4
   std::vector<int64_t> off;      // per frame: depth offset in its half (colour follows)
   std::vector<int64_t> bytes;    // per frame: depth bytes
 };
@@ -595,8 +597,9 @@ tsdf_status stage_sub_batch(void* ctx, int b, int f0, int nf, cudaStream_t sa) {
   tsdf_map* lead = h.lead;
   std::vector<FrameDev>& fr = *h.fr;
   cudaStream_t c = lead->copy;
-  if (b >= 2 && cudaStreamWaitEvent(c, lead->ev_int[(b - 2) & 3], 0) != cudaSuccess) return cuda_fail();
-  char* half = h.base + (int64_t)(b & 1) * h.half;
+  if (b >= h.slots && cudaStreamWaitEvent(c, lead->ev_int[(b - h.slots) & 3], 0) != cudaSuccess)
+    return cuda_fail();
+  char* half = h.base + (int64_t)(b % h.slots) * h.half;
   // copy runs of frames whose images are contiguous both on the host and in the half
   int f = f0;
   while (f < f0 + nf) {
@@ -665,6 +668,7 @@ tsdf_status integrate_batch_host(tsdf_map* const* maps, int32_t n_maps, const ts
   }
   h.half = align256(need);
   if (2 * h.half > staging_bytes) return TSDF_ERR_ARG;  // two sub-batches must fit
+  h.slots = (int)std::min<int64_t>(4, staging_bytes / h.half);
   tsdf_map* lead = maps[0];
   if (!lead->copy) {
     bool ok = cudaStreamCreateWithFlags(&lead->copy, cudaStreamNonBlocking) == cudaSuccess;

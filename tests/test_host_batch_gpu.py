@@ -35,8 +35,9 @@ def _device_batch(w, frames, **kw):
     return out
 
 
-@pytest.mark.parametrize("layout", ["contiguous", "scattered"])
-def test_host_batch_equals_device_batch(room, layout):
+@pytest.mark.parametrize("layout,slots", [("contiguous", 2), ("scattered", 2), ("contiguous", 3),
+                                          ("scattered", 4)])
+def test_host_batch_equals_device_batch(room, layout, slots):
     w, frames = room
     ref = _device_batch(w, frames)
     if layout == "contiguous":
@@ -45,7 +46,7 @@ def test_host_batch_equals_device_batch(room, layout):
     else:
         imgs = [torch.from_numpy(np.ascontiguousarray(f.depth)).pin_memory() for f in frames]
     m = gt.TsdfMap(w.voxel_size)
-    staging = torch.empty(2 * 32 * 640 * 480 * 4, dtype=torch.uint8, device="cuda")
+    staging = torch.empty(slots * 32 * 640 * 480 * 4, dtype=torch.uint8, device="cuda")
     descs = [gt.frame_desc_host(0, f.sensor, f.T, d) for f, d in zip(frames, imgs)]
     gt.integrate_batch_host([m.handle], descs, staging)
     # a second call reuses the staging buffer after the first one's work
