@@ -90,6 +90,22 @@ __device__ __forceinline__ void tsdf_at(const MapDev& m, uint32_t p, int l, floa
   }
 }
 
+// Hashed bitmaps of the blocks where a site disappeared (lost-site blocks)
+// and of their coarse cells (cubes of G = R + 1 blocks, R the reach of a
+// parent in blocks), written by the mark stage for the clear stage.
+constexpr int kNearBits = kEsdfBitWords * 32;
+constexpr int kCoordBias = 1 << 21;  // block coordinates + bias >= 0
+
+__device__ __forceinline__ uint32_t near_bit(int cx, int cy, int cz) {
+  return ((uint32_t)cx * 73856093u ^ (uint32_t)cy * 19349663u ^ (uint32_t)cz * 83492791u) & (kNearBits - 1);
+}
+
+__device__ __forceinline__ int parent_reach(const EsdfDev& e) { return (e.max_dist + 7) / 8 + 1; }
+
+__device__ __forceinline__ bool bit_set(const uint32_t* bits, uint32_t b) {
+  return (__ldg(bits + (b >> 5)) >> (b & 31)) & 1u;
+}
+
 // ------------------------------------------------------------- mark sites
 
 __global__ void __launch_bounds__(kEsdfThreads)
@@ -130,45 +146,48 @@ __global__ void __launch_bounds__(kEsdfThreads)
     if (t == 0) {
       m.dirty[p] &= (uint8_t)~kDirtyEsdf;
       if (any) add_update(e, e.list[0], e.cnt, p, gen);
-      if (lost) e.clist[atomicAdd(e.cnt + 2, 1u)] = p;
+      if (lost) {
+        e.clist[atomicAdd(e.cnt + 2, 1u)] = p;
+        const unsigned long long key = m.block_keys[p];
+        const int G = parent_reach(e) + 1;
+        const int cx = key_coord(key, 0) + kCoordBias, cy = key_coord(key, 1) + kCoordBias,
+                  cz = key_coord(key, 2) + kCoordBias;
+        const uint32_t l = near_bit(cx, cy, cz), c = near_bit(cx / G, cy / G, cz / G);
+        atomicOr(e.bits + (l >> 5), 1u << (l & 31));
+        atomicOr(e.bits + kEsdfBitWords + (c >> 5), 1u << (c & 31));
+      }
     }
   }
 }
 
 // ---------------------------------------------------------- clear invalid
 
-constexpr int kClearChunk = 512;
-
+// Between updates every parent is a site, and sites disappear only in the
+// lost-site blocks.  A block is checked if a marked coarse cell is among the
+// 27 around its own (every block within R of a lost-site block is), and in
+// it a parent is looked up only if its block's bit is set.  Bitmap
+// collisions only add checks of parents that are still sites, which change
+// nothing.
 __global__ void __launch_bounds__(kEsdfThreads)
     esdf_clear_kernel(const MapDev m, const EsdfDev e, uint32_t gen) {
-  __shared__ int s_c[kClearChunk][3];
   const uint32_t nc = __ldcg(e.cnt + 2);
   if (nc == 0) return;
   const uint32_t nb = n_blocks(m);
   const int t = threadIdx.x;
-  const int R = (e.max_dist + 7) / 8 + 1;
+  const int G = parent_reach(e) + 1;  // coarse cell edge in blocks
+  const uint32_t* lost_bits = e.bits;
+  const uint32_t* cell_bits = e.bits + kEsdfBitWords;
   unsigned long long my_cleared = 0;
   for (uint32_t p = blockIdx.x; p < nb; p += gridDim.x) {
     const unsigned long long key = m.block_keys[p];
     const int bx = key_coord(key, 0), by = key_coord(key, 1), bz = key_coord(key, 2);
     bool near = false;
-    for (uint32_t c0 = 0; c0 < nc; c0 += kClearChunk) {
-      const uint32_t cn = min((uint32_t)kClearChunk, nc - c0);
-      __syncthreads();
-      for (uint32_t i = t; i < cn; i += kEsdfThreads) {
-        const unsigned long long ck = m.block_keys[e.clist[c0 + i]];
-        s_c[i][0] = key_coord(ck, 0);
-        s_c[i][1] = key_coord(ck, 1);
-        s_c[i][2] = key_coord(ck, 2);
-      }
-      __syncthreads();
-      for (uint32_t i = t; i < cn && !near; i += kEsdfThreads)
-        near = abs(bx - s_c[i][0]) <= R && abs(by - s_c[i][1]) <= R && abs(bz - s_c[i][2]) <= R;
-      if (__syncthreads_or(near)) {
-        near = true;
-        break;
-      }
+    if (t < 27) {
+      const uint32_t b = near_bit((bx + kCoordBias) / G + t % 3 - 1, (by + kCoordBias) / G + (t / 3) % 3 - 1,
+                                  (bz + kCoordBias) / G + t / 9 - 1);
+      near = bit_set(cell_bits, b);
     }
+    near = __syncthreads_or(near);
     if (!near) continue;  // uniform: set by __syncthreads_or
     bool any = false;
 #pragma unroll
@@ -182,6 +201,8 @@ __global__ void __launch_bounds__(kEsdfThreads)
       const int gy = 8 * by + ((l >> 3) & 7) + off_comp(s, 1);
       const int gz = 8 * bz + (l >> 6) + off_comp(s, 2);
       const int pbx = gx >> 3, pby = gy >> 3, pbz = gz >> 3;
+      const uint32_t lb = near_bit(pbx + kCoordBias, pby + kCoordBias, pbz + kCoordBias);
+      if (!bit_set(lost_bits, lb)) continue;  // its block lost no site
       const int pp = (pbx == bx && pby == by && pbz == bz) ? (int)p : pool_of(m, pbx, pby, pbz);
       const bool ok = pp >= 0 &&
                       (e.st[(size_t)pp * 512 + (gx & 7) + 8 * (gy & 7) + 64 * (gz & 7)] & kEsdfSite);
@@ -212,15 +233,68 @@ __global__ void esdf_nbr_kernel(const MapDev m, const EsdfDev e) {
   }
 }
 
-// Six in-block sweeps of every block of the current update set.  64 threads
-// sweep the 64 lines of an axis direction, one line each.  Afterwards the
-// block and its existing face neighbours join this iteration's tlist.
-// Thread 0 of CTA 0 zeroes the next update set's size first (that set was
-// consumed by the previous iteration).
+// In-block sweeps keep the block in shared memory padded to 9 words per
+// x-row and 72 per z-slice, so that the lines of every axis are read with at
+// most two-way bank conflicts, with each voxel's squared parent distance
+// beside its state.
+constexpr int kSweepRow = 9, kSweepSlice = 72;
+constexpr int kSweepWords = 7 + 7 * kSweepRow + 7 * kSweepSlice + 1;
+
+__device__ __forceinline__ int sweep_idx(int l) {
+  return (l & 7) + kSweepRow * ((l >> 3) & 7) + kSweepSlice * (l >> 6);
+}
+
+// relax() for a neighbour q on axis AXIS at p + D (D = +-1), with the squared
+// lengths carried along: q's candidate offset differs from q's own in the
+// AXIS component only, so its squared length is q2 + 2 D o + 1.  Same
+// decisions and the same resulting state as relax().
+template <int AXIS, int D>
+__device__ __forceinline__ void relax_line(uint32_t& ps, int& p2, uint32_t qs, int q2, int max2) {
+  const int oq = off_comp(qs, AXIS);
+  const int c2 = q2 + 2 * D * oq + 1;
+  const bool take = (ps & (kEsdfObs | kEsdfSite)) == kEsdfObs && (qs & kEsdfPar) && c2 <= max2 &&
+                    (!(ps & kEsdfPar) || c2 < p2);
+  if (take) {
+    ps = (ps & ~kEsdfOffMask) | kEsdfPar | (qs & kEsdfOffMask & ~(511u << (9 * AXIS))) |
+         (((uint32_t)(oq + D) & 511u) << (9 * AXIS));
+    p2 = c2;
+  }
+}
+
+// Both sweeps along AXIS of one line of eight voxels (first i = 1 .. 7, each
+// voxel trying its predecessor's parent, then i = 6 .. 0, each trying its
+// successor's), in registers.
+template <int AXIS>
+__device__ __forceinline__ void sweep_line(uint32_t* s, int* s2, int base, int max2) {
+  constexpr int stride = AXIS == 0 ? 1 : (AXIS == 1 ? kSweepRow : kSweepSlice);
+  uint32_t w[8];
+  int d2[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    w[i] = s[base + stride * i];
+    d2[i] = s2[base + stride * i];
+  }
+#pragma unroll
+  for (int i = 1; i < 8; ++i) relax_line<AXIS, -1>(w[i], d2[i], w[i - 1], d2[i - 1], max2);
+#pragma unroll
+  for (int i = 6; i >= 0; --i) relax_line<AXIS, 1>(w[i], d2[i], w[i + 1], d2[i + 1], max2);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    s[base + stride * i] = w[i];
+    s2[base + stride * i] = d2[i];
+  }
+}
+
+// Six in-block sweeps of every block of the current update set (+x, -x,
+// +y, -y, +z, -z).  64 threads sweep the 64 lines of an axis, one line
+// each.  Afterwards the block and its existing face neighbours join this
+// iteration's tlist.  Thread 0 of CTA 0 zeroes the next update set's size
+// first (that set was consumed by the previous iteration).
 __global__ void __launch_bounds__(64)
     esdf_sweep_kernel(const EsdfDev e, const uint32_t* __restrict__ list, const uint32_t* size,
                       uint32_t* zero_next, uint32_t* tlist, uint32_t* tsize, uint32_t gen_t) {
-  __shared__ uint32_t s[512];
+  __shared__ uint32_t s[kSweepWords];
+  __shared__ int s2[kSweepWords];
   const uint32_t n = __ldcg(size);
   const int t = threadIdx.x;
   if (blockIdx.x == 0 && t == 0) {
@@ -231,34 +305,26 @@ __global__ void __launch_bounds__(64)
     }
   }
   const int max2 = e.max_dist * e.max_dist;
+  const int a = t & 7, c = t >> 3;  // the line's coordinates on the two other axes, in axis order
   for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
     const uint32_t p = list[k];
     uint32_t* g = e.st + (size_t)p * 512;
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 8; ++i) s[t + 64 * i] = g[t + 64 * i];
-    __syncthreads();
-    const int a = t & 7, c = t >> 3;  // coordinates on the two other axes, in axis order
-#pragma unroll
-    for (int axis = 0; axis < 3; ++axis) {
-      // linear index of position i along `axis` on this thread's line
-      const int stride = axis == 0 ? 1 : (axis == 1 ? 8 : 64);
-      const int base = axis == 0 ? 8 * a + 64 * c : (axis == 1 ? a + 64 * c : a + 8 * c);
-#pragma unroll
-      for (int dir = 0; dir < 2; ++dir) {
-        const int step = dir == 0 ? -1 : 1;  // position of the previous voxel relative to i
-#pragma unroll
-        for (int k2 = 1; k2 < 8; ++k2) {
-          const int i = dir == 0 ? k2 : 7 - k2;
-          const int j = i + step;
-          relax(s[base + stride * i], s[base + stride * j], axis == 0 ? step : 0,
-                axis == 1 ? step : 0, axis == 2 ? step : 0, max2);
-        }
-        __syncthreads();
-      }
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t v = g[t + 64 * i];
+      s[sweep_idx(t + 64 * i)] = v;
+      s2[sweep_idx(t + 64 * i)] = dist2(v);
     }
+    __syncthreads();
+    sweep_line<0>(s, s2, kSweepRow * a + kSweepSlice * c, max2);
+    __syncthreads();
+    sweep_line<1>(s, s2, a + kSweepSlice * c, max2);
+    __syncthreads();
+    sweep_line<2>(s, s2, a + kSweepRow * c, max2);
+    __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 8; ++i) g[t + 64 * i] = s[t + 64 * i];
+    for (int i = 0; i < 8; ++i) g[t + 64 * i] = s[sweep_idx(t + 64 * i)];
     if (t < 7) {
       const int q = t == 6 ? (int)p : e.nbr[6 * (size_t)p + t];
       if (q >= 0 && atomicExch(e.stamp_t + q, gen_t) != gen_t) tlist[atomicAdd(tsize, 1u)] = (uint32_t)q;
@@ -440,9 +506,11 @@ cudaError_t launch_esdf_iteration(const MapDev& m, const EsdfDev& e, int cur, ui
   uint32_t* next = cur ? e.list[0] : e.list[1];
   uint32_t* tl = cur ? e.tlist[1] : e.tlist[0];
   uint32_t* tsize = e.cnt + 3 + cur;
-  esdf_sweep_kernel<<<grid_for(16), 64, 0, s>>>(e, list, e.cnt + cur, e.cnt + (1 - cur), tl, tsize, gen_t);
-  esdf_pull_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(e, tl, tsize);
-  esdf_apply_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(e, tl, tsize, e.cnt + 3 + (1 - cur), next,
+  // latency-bound stages: enough resident warps per SM to overlap the
+  // blocks' loads (sweep 40 registers x 64 threads, pull 32 x 128)
+  esdf_sweep_kernel<<<grid_for(24), 64, 0, s>>>(e, list, e.cnt + cur, e.cnt + (1 - cur), tl, tsize, gen_t);
+  esdf_pull_kernel<<<grid_for(16), kEsdfThreads, 0, s>>>(e, tl, tsize);
+  esdf_apply_kernel<<<grid_for(16), kEsdfThreads, 0, s>>>(e, tl, tsize, e.cnt + 3 + (1 - cur), next,
                                                           e.cnt + (1 - cur), gen_next);
   (void)m;
   return cudaGetLastError();

@@ -305,6 +305,7 @@ void free_map(tsdf_map* m) {
     cudaFree(m->esdf.stamp_s);
     cudaFree(m->esdf.stamp_t);
     cudaFree(m->esdf.tchanged);
+    cudaFree(m->esdf.bits);
     cudaFree(m->esdf.cnt);
     cudaFree(m->esdf.stats);
     cudaFreeHost(m->esdf_host);
@@ -894,6 +895,7 @@ tsdf_status esdf_alloc(tsdf_map* m, const tsdf_esdf_opts& o) {
             cudaMalloc(&e.stamp_s, sizeof(uint32_t) * nb) == cudaSuccess &&
             cudaMalloc(&e.stamp_t, sizeof(uint32_t) * nb) == cudaSuccess &&
             cudaMalloc(&e.tchanged, nb) == cudaSuccess &&
+            cudaMalloc(&e.bits, sizeof(uint32_t) * 2 * gbt::kEsdfBitWords) == cudaSuccess &&
             cudaMalloc(&e.cnt, sizeof(uint32_t) * 8) == cudaSuccess &&
             cudaMalloc(&e.stats, sizeof(unsigned long long) * 4) == cudaSuccess &&
             cudaMallocHost(&m->esdf_host, sizeof(uint32_t) * 8) == cudaSuccess;
@@ -945,6 +947,7 @@ tsdf_status map_esdf_update(tsdf_map* map, const tsdf_esdf_opts* opts, void* cud
   // mark sites and clear invalid parents: update set 0 gets generation g
   const uint32_t g = ++map->esdf_gen;
   if (cudaMemsetAsync(e.cnt, 0, sizeof(uint32_t) * 8, s) != cudaSuccess ||
+      cudaMemsetAsync(e.bits, 0, sizeof(uint32_t) * 2 * gbt::kEsdfBitWords, s) != cudaSuccess ||
       gbt::launch_esdf_mark(map->dev, e, g, s) != cudaSuccess ||
       gbt::launch_esdf_clear(map->dev, e, g, s) != cudaSuccess)
     return cuda_fail();

@@ -86,6 +86,7 @@ enum : uint8_t { kDirtyEsdf = 1, kDirtyMesh = 2 };
 constexpr uint32_t kEsdfObs = 1u << 27, kEsdfSite = 1u << 28, kEsdfPar = 1u << 29,
                    kEsdfInside = 1u << 30;
 constexpr uint32_t kEsdfOffMask = (1u << 27) - 1u;
+constexpr int kEsdfBitWords = (1 << 16) / 32;
 struct EsdfDev {
   uint32_t* st;         // [max_blocks][512] voxel states
   uint32_t* st2;        // [max_blocks][512] states produced by a face exchange
@@ -98,6 +99,8 @@ struct EsdfDev {
   uint8_t* tchanged;    // [max_blocks] per tlist entry: the exchange changed the block
   int32_t* nbr;         // [max_blocks][6] pool index of each face neighbour (-x, +x, -y,
                         // +y, -z, +z), -1 if none; rebuilt by every update
+  uint32_t* bits;       // [2][kEsdfBitWords] hashed bitmaps of the clist blocks and of their
+                        // coarse cells, rebuilt by every update
   uint32_t* cnt;        // [0], [1] update set sizes, [2] clist size, [3], [4] tlist sizes
   unsigned long long* stats;    // [0] voxels whose parent stopped being a site, [1] lowering
                                 // iterations, [2] blocks swept, [3] blocks in face exchanges
