@@ -168,53 +168,64 @@ __global__ void __launch_bounds__(kEsdfThreads)
 // it a parent is looked up only if its block's bit is set.  Bitmap
 // collisions only add checks of parents that are still sites, which change
 // nothing.
+// One warp per pool block, 16 voxels per lane (voxels 128 j + 4 lane + i).
 __global__ void __launch_bounds__(kEsdfThreads)
     esdf_clear_kernel(const MapDev m, const EsdfDev e, uint32_t gen) {
+  constexpr int kWarps = kEsdfThreads / 32;
   const uint32_t nc = __ldcg(e.cnt + 2);
   if (nc == 0) return;
   const uint32_t nb = n_blocks(m);
-  const int t = threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = parent_reach(e) + 1;  // coarse cell edge in blocks
   const uint32_t* lost_bits = e.bits;
   const uint32_t* cell_bits = e.bits + kEsdfBitWords;
   unsigned long long my_cleared = 0;
-  for (uint32_t p = blockIdx.x; p < nb; p += gridDim.x) {
+  for (uint32_t p = blockIdx.x * kWarps + warp; p < nb; p += gridDim.x * kWarps) {
     const unsigned long long key = m.block_keys[p];
     const int bx = key_coord(key, 0), by = key_coord(key, 1), bz = key_coord(key, 2);
     bool near = false;
-    if (t < 27) {
-      const uint32_t b = near_bit((bx + kCoordBias) / G + t % 3 - 1, (by + kCoordBias) / G + (t / 3) % 3 - 1,
-                                  (bz + kCoordBias) / G + t / 9 - 1);
+    if (lane < 27) {
+      const uint32_t b = near_bit((bx + kCoordBias) / G + lane % 3 - 1, (by + kCoordBias) / G + (lane / 3) % 3 - 1,
+                                  (bz + kCoordBias) / G + lane / 9 - 1);
       near = bit_set(cell_bits, b);
     }
-    near = __syncthreads_or(near);
-    if (!near) continue;  // uniform: set by __syncthreads_or
+    if (!__any_sync(0xffffffffu, near)) continue;
+    uint4* blk = reinterpret_cast<uint4*>(e.st + (size_t)p * 512) + lane;
+    uint32_t v[16];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint4 a = blk[32 * j];
+      v[4 * j] = a.x; v[4 * j + 1] = a.y; v[4 * j + 2] = a.z; v[4 * j + 3] = a.w;
+    }
     bool any = false;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int l = 4 * t + i;
-      uint32_t* sp = e.st + (size_t)p * 512 + l;
-      const uint32_t s = *sp;
-      if (!(s & kEsdfPar) || (s & kEsdfSite)) continue;
-      // parent voxel in global voxel coordinates, then its block and index
-      const int gx = 8 * bx + (l & 7) + off_comp(s, 0);
-      const int gy = 8 * by + ((l >> 3) & 7) + off_comp(s, 1);
-      const int gz = 8 * bz + (l >> 6) + off_comp(s, 2);
-      const int pbx = gx >> 3, pby = gy >> 3, pbz = gz >> 3;
-      const uint32_t lb = near_bit(pbx + kCoordBias, pby + kCoordBias, pbz + kCoordBias);
-      if (!bit_set(lost_bits, lb)) continue;  // its block lost no site
-      const int pp = (pbx == bx && pby == by && pbz == bz) ? (int)p : pool_of(m, pbx, pby, pbz);
-      const bool ok = pp >= 0 &&
-                      (e.st[(size_t)pp * 512 + (gx & 7) + 8 * (gy & 7) + 64 * (gz & 7)] & kEsdfSite);
-      if (!ok) {
-        *sp = s & ~(kEsdfPar | kEsdfOffMask);
-        ++my_cleared;
-        any = true;
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int l = 128 * j + 4 * lane + i;
+        const uint32_t s = v[4 * j + i];
+        if (!(s & kEsdfPar) || (s & kEsdfSite)) continue;
+        // parent voxel in global voxel coordinates, then its block and index
+        const int gx = 8 * bx + (l & 7) + off_comp(s, 0);
+        const int gy = 8 * by + ((l >> 3) & 7) + off_comp(s, 1);
+        const int gz = 8 * bz + (l >> 6) + off_comp(s, 2);
+        const int pbx = gx >> 3, pby = gy >> 3, pbz = gz >> 3;
+        const uint32_t lb = near_bit(pbx + kCoordBias, pby + kCoordBias, pbz + kCoordBias);
+        if (!bit_set(lost_bits, lb)) continue;  // its block lost no site
+        const int pp = (pbx == bx && pby == by && pbz == bz) ? (int)p : pool_of(m, pbx, pby, pbz);
+        const bool ok = pp >= 0 &&
+                        (e.st[(size_t)pp * 512 + (gx & 7) + 8 * (gy & 7) + 64 * (gz & 7)] & kEsdfSite);
+        if (!ok) {
+          e.st[(size_t)p * 512 + l] = s & ~(kEsdfPar | kEsdfOffMask);
+          ++my_cleared;
+          any = true;
+        }
       }
-    }
-    if (__syncthreads_or(any) && t == 0) add_update(e, e.list[0], e.cnt, p, gen);
+    if (__any_sync(0xffffffffu, any) && lane == 0) add_update(e, e.list[0], e.cnt, p, gen);
   }
-  if (my_cleared) atomicAdd(e.stats, my_cleared);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_cleared += __shfl_down_sync(0xffffffffu, my_cleared, o);
+  if (lane == 0 && my_cleared) atomicAdd(e.stats, my_cleared);
 }
 
 // ------------------------------------------------------------ lower ESDF
@@ -492,7 +503,7 @@ cudaError_t launch_esdf_mark(const MapDev& m, const EsdfDev& e, uint32_t gen, cu
 }
 
 cudaError_t launch_esdf_clear(const MapDev& m, const EsdfDev& e, uint32_t gen, cudaStream_t s) {
-  esdf_clear_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(m, e, gen);
+  esdf_clear_kernel<<<grid_for(10), kEsdfThreads, 0, s>>>(m, e, gen);  // 48 registers: 10 CTAs per SM
   esdf_nbr_kernel<<<grid_for(4), 256, 0, s>>>(m, e);
   return cudaGetLastError();
 }
