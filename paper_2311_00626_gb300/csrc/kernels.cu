@@ -344,63 +344,13 @@ __device__ __forceinline__ float atan2_dec(float y, float x) {
   return a;
 }
 
-__device__ __forceinline__ bool lidar_valid(const FrameDev& F, float d) {
-  return d >= F.min_range && d <= F.max_range;
+// Azimuth column k in [-1, naz] wrapped into [0, naz).
+__device__ __forceinline__ int wrap_az(int k, int naz) {
+  return k < 0 ? k + naz : (k >= naz ? k - naz : k);
 }
 
-// Sample the image at the projection of sensor-frame point (px, py, pz).
-// Returns false if the voxel is not updated; else the depth sample d and the
-// voxel depth d_v (z for a camera, range for a LiDAR).  Eq. 1-3.
-__device__ __forceinline__ bool sample(const FrameDev& F, const MapDev& m, float px, float py,
-                                       float pz, float& d, float& dv) {
-  if (F.kind == kSensorPinhole) {
-    if (!(pz > 0.0f)) return false;
-    const float iz = __frcp_rn(pz);
-    const float u = __fadd_rn(__fmaf_rn(__fmul_rn(px, iz), F.fu, F.cu), 0.5f);
-    const float v = __fadd_rn(__fmaf_rn(__fmul_rn(py, iz), F.fv, F.cv), 0.5f);
-    if (!(u >= 0.0f && u < (float)F.width && v >= 0.0f && v < (float)F.height)) return false;
-    d = __ldg(F.depth + (int)v * F.width + (int)u);
-    if (!(d > 0.0f && d <= FLT_MAX)) return false;
-    dv = pz;
-    return true;
-  }
-  const float r = __fsqrt_rn(__fmaf_rn(px, px, __fmaf_rn(py, py, __fmul_rn(pz, pz))));
-  if (!(r > 0.0f)) return false;
-  const float rho = __fsqrt_rn(__fmaf_rn(px, px, __fmul_rn(py, py)));
-  const float th = atan2_dec(py, px);
-  const float ph = atan2_dec(rho, pz);
-  const float u = __fmul_rn(__fsub_rn(th, F.theta_start), F.alpha);
-  const float v = __fmul_rn(__fsub_rn(ph, F.phi_start), F.beta);
-  const int naz = F.width, nel = F.height;
-  if (m.lidar_nearest) {
-    const float ku = floorf(u), jv = floorf(v);
-    if (!(jv >= 0.0f && jv <= (float)(nel - 1))) return false;
-    if (!(ku >= -1.0f && ku <= (float)naz)) return false;
-    const int kk = (((int)ku % naz) + naz) % naz, jj = (int)jv;
-    d = __ldg(F.depth + jj * naz + kk);
-    if (!lidar_valid(F, d)) return false;
-  } else {
-    const float uu = __fsub_rn(u, 0.5f), vv = __fsub_rn(v, 0.5f);
-    const float k0f = floorf(uu), j0f = floorf(vv);
-    if (!(j0f >= 0.0f && j0f <= (float)(nel - 2))) return false;
-    if (!(k0f >= -1.0f && k0f <= (float)naz)) return false;
-    const float fx = __fsub_rn(uu, k0f), fy = __fsub_rn(vv, j0f);
-    const int k0 = (((int)k0f % naz) + naz) % naz, k1 = (k0 + 1) % naz, j0 = (int)j0f;
-    const float* row0 = F.depth + j0 * naz;
-    const float* row1 = row0 + naz;
-    const float d00 = __ldg(row0 + k0), d10 = __ldg(row0 + k1);
-    const float d01 = __ldg(row1 + k0), d11 = __ldg(row1 + k1);
-    if (!(lidar_valid(F, d00) && lidar_valid(F, d10) && lidar_valid(F, d01) && lidar_valid(F, d11)))
-      return false;
-    const float hi = fmaxf(fmaxf(d00, d10), fmaxf(d01, d11));
-    const float lo = fminf(fminf(d00, d10), fminf(d01, d11));
-    if (__fsub_rn(hi, lo) > m.guard) return false;
-    const float top = __fmaf_rn(fx, __fsub_rn(d10, d00), d00);
-    const float bot = __fmaf_rn(fx, __fsub_rn(d11, d01), d01);
-    d = __fmaf_rn(fy, __fsub_rn(bot, top), top);
-  }
-  dv = r;
-  return true;
+__device__ __forceinline__ bool lidar_valid(const FrameDev& F, float d) {
+  return d >= F.min_range && d <= F.max_range;
 }
 
 // TSDF update functor (Sec. IV-B): weighted running average, the average
@@ -673,21 +623,73 @@ __device__ __forceinline__ void fuse_pinhole(const P& p, const FrameProj* s_fp, 
     }
 }
 
-// One frame of any sensor kind, voxel by voxel (colour layers take pinhole
-// frames only, through fuse_pinhole).
+// A LiDAR frame (Eq. 1 and 3): phase 1 finds every voxel's beam cell and
+// issues its range loads (the four around it, or the nearest one), phase 2
+// applies the guarded bilinear sample and the updates.  A voxel at the
+// sensor origin, outside the elevation rows or with an invalid sample is not
+// updated; azimuth wraps.  Colour layers take pinhole frames only.
 template <int STORAGE, bool WEIGHTED>
-__device__ __forceinline__ void fuse_any(const FrameDev& F, const MapDev& m, const VoxelRow& r,
-                                         float* D, float* W, unsigned long long& upd) {
+__device__ __forceinline__ void fuse_lidar(const FrameDev& F, const MapDev& m, const VoxelRow& r,
+                                           float* D, float* W, unsigned long long& upd) {
   if (STORAGE == kStorageColor) return;
   float px[4], py[4], pz[4];
   row_points(F, m.v, r, px, py, pz);
+  const int naz = F.width, nel = F.height;
+  float rr[4], fx[4], fy[4], d00[4], d10[4], d01[4], d11[4];
+  bool ok[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    float d, dv;
-    if (!sample(F, m, px[i], py[i], pz[i], d, dv)) continue;
-    const float dp = __fsub_rn(d, dv);
+    rr[i] = __fsqrt_rn(__fmaf_rn(px[i], px[i], __fmaf_rn(py[i], py[i], __fmul_rn(pz[i], pz[i]))));
+    const float rho = __fsqrt_rn(__fmaf_rn(px[i], px[i], __fmul_rn(py[i], py[i])));
+    const float th = atan2_dec(py[i], px[i]);
+    const float ph = atan2_dec(rho, pz[i]);
+    const float u = __fmul_rn(__fsub_rn(th, F.theta_start), F.alpha);
+    const float v = __fmul_rn(__fsub_rn(ph, F.phi_start), F.beta);
+    ok[i] = rr[i] > 0.0f;
+    d00[i] = d10[i] = d01[i] = d11[i] = 0.0f;
+    if (m.lidar_nearest) {
+      const float ku = floorf(u), jv = floorf(v);
+      fx[i] = fy[i] = 0.0f;
+      ok[i] = ok[i] && jv >= 0.0f && jv <= (float)(nel - 1) && ku >= -1.0f && ku <= (float)naz;
+      if (ok[i]) d00[i] = __ldg(F.depth + (int)jv * naz + wrap_az((int)ku, naz));
+    } else {
+      const float uu = __fsub_rn(u, 0.5f), vv = __fsub_rn(v, 0.5f);
+      const float k0f = floorf(uu), j0f = floorf(vv);
+      fx[i] = __fsub_rn(uu, k0f);
+      fy[i] = __fsub_rn(vv, j0f);
+      ok[i] = ok[i] && j0f >= 0.0f && j0f <= (float)(nel - 2) && k0f >= -1.0f && k0f <= (float)naz;
+      if (ok[i]) {
+        const int k0 = wrap_az((int)k0f, naz), k1 = k0 + 1 == naz ? 0 : k0 + 1;
+        const float* row0 = F.depth + (int)j0f * naz;
+        const float* row1 = row0 + naz;
+        d00[i] = __ldg(row0 + k0);
+        d10[i] = __ldg(row0 + k1);
+        d01[i] = __ldg(row1 + k0);
+        d11[i] = __ldg(row1 + k1);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (!ok[i]) continue;
+    float d;
+    if (m.lidar_nearest) {
+      d = d00[i];
+      if (!lidar_valid(F, d)) continue;
+    } else {
+      if (!(lidar_valid(F, d00[i]) && lidar_valid(F, d10[i]) && lidar_valid(F, d01[i]) &&
+            lidar_valid(F, d11[i])))
+        continue;
+      const float hi = fmaxf(fmaxf(d00[i], d10[i]), fmaxf(d01[i], d11[i]));
+      const float lo = fminf(fminf(d00[i], d10[i]), fminf(d01[i], d11[i]));
+      if (__fsub_rn(hi, lo) > m.guard) continue;
+      const float top = __fmaf_rn(fx[i], __fsub_rn(d10[i], d00[i]), d00[i]);
+      const float bot = __fmaf_rn(fx[i], __fsub_rn(d11[i], d01[i]), d01[i]);
+      d = __fmaf_rn(fy[i], __fsub_rn(bot, top), top);
+    }
+    const float dp = __fsub_rn(d, rr[i]);
     if (dp < -m.tau) continue;
-    apply<STORAGE, WEIGHTED>(m, D[i], W[i], dv, dp);
+    apply<STORAGE, WEIGHTED>(m, D[i], W[i], rr[i], dp);
     ++upd;
   }
 }
@@ -776,7 +778,7 @@ __global__ void __launch_bounds__(kIntegrateThreads)
         else if (!PINHOLE_ONLY) {
           const int f = __ffs(bits) - 1;  // a LiDAR frame
           bits &= bits - 1u;
-          fuse_any<STORAGE, WEIGHTED>(p.fr[f], m, vr, D, W, my_upd);
+          fuse_lidar<STORAGE, WEIGHTED>(p.fr[f], m, vr, D, W, my_upd);
         }
       }
       Voxels4<STORAGE>::store(m, pool, t, D, W, G, B);
