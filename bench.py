@@ -815,9 +815,14 @@ def bench_serving(args):
             cache[key] = torch.from_numpy(d).pin_memory()
         reqs.append(Request(len(reqs), mid, sensor, T, cache[key], t))
 
+    # the maps persist across runs (reset in between), so that per-map set-up
+    # (sensor tables, the copy stream) stays outside the timed runs
+    maps = [gt.TsdfMap(c["voxel_size"], c["truncation_voxels"], c["max_weight"],
+                       storage=gt.STORAGE_FP16) for c in cfg]
+
     def serve(paced):
-        maps = [gt.TsdfMap(c["voxel_size"], c["truncation_voxels"], c["max_weight"],
-                           storage=gt.STORAGE_FP16) for c in cfg]
+        for m in maps:
+            m.reset()
         rs = [Request(r.rid, r.map_id, r.sensor, r.T, r.depth, r.arrival if paced else 0.0)
               for r in reqs]
         srv = Server(maps, staging_bytes=512 << 20, max_frames=32)
@@ -826,18 +831,21 @@ def bench_serving(args):
         done = srv.run(rs, paced=paced)
         wall = time.perf_counter() - t0
         upd = sum(m.stats()["voxel_updates"] for m in maps)
-        for m in maps:
-            m.close()
         return {"wall_s": wall, "voxel_updates": upd, "launches": srv.launches,
                 **Server.latency_stats(done)}
 
-    serve(False)  # warm-up (LiDAR tables, allocator)
-    unpaced = serve(False)
+    for _ in range(args.warmup):
+        serve(False)
+    runs = sorted((serve(False) for _ in range(3)), key=lambda r: r["wall_s"])
+    unpaced = runs[1]  # the median of three
+    unpaced["wall_s_runs"] = [r["wall_s"] for r in runs]
     paced = serve(True)
+    for m in maps:
+        m.close()
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": ws * unpaced["voxel_updates"] / unpaced["wall_s"],
-            "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": 1,
+            "unit": UNIT, "n_gpus": ws, "steps": 3, "warmup": args.warmup,
             "ms_per_step": unpaced["wall_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"serving: 16 maps, Poisson 30 Hz per map for {args.serve_seconds} s "
