@@ -153,10 +153,30 @@ def _pose(T) -> ctypes.Array:
     return (ctypes.c_double * 16)(*a.tolist())
 
 
+def _pose_arg(T):
+    """A pose as a call argument: the array's own memory when it already is
+    16 contiguous doubles (the caller holds it for the call), else a copy."""
+    if type(T) is np.ndarray and T.dtype == np.float64 and T.size == 16 and T.flags.c_contiguous:
+        return T.ctypes.data
+    return _pose(T)
+
+
+_torch = None
+_raw_stream = None
+
+
 def _stream(stream) -> int | None:
+    """The CUDA stream handle of `stream`, or of torch's current stream."""
+    global _torch, _raw_stream
     if stream is None:
-        import torch
-        return torch.cuda.current_stream().cuda_stream
+        if _torch is None:
+            import torch
+            _torch = torch
+            # the raw getter avoids building a Stream object on every call
+            _raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+        if _raw_stream is not None:
+            return _raw_stream(_torch._C._cuda_getDevice())
+        return _torch.cuda.current_stream().cuda_stream
     return int(stream) if not hasattr(stream, "cuda_stream") else stream.cuda_stream
 
 
@@ -201,12 +221,12 @@ def map_create_ex(voxel_size, truncation_voxels, max_weight, storage=STORAGE_FP3
 
 
 def integrate_depth(m: int, depth, intr: Pinhole, T_world_cam, stream=None):
-    _check(lib().integrate_depth(m, _dptr(depth), ctypes.byref(intr), _pose(T_world_cam),
+    _check(lib().integrate_depth(m, _dptr(depth), ctypes.byref(intr), _pose_arg(T_world_cam),
                                  _stream(stream)), "integrate_depth")
 
 
 def integrate_lidar(m: int, rng, intr: Lidar, T_world_lidar, stream=None):
-    _check(lib().integrate_lidar(m, _dptr(rng), ctypes.byref(intr), _pose(T_world_lidar),
+    _check(lib().integrate_lidar(m, _dptr(rng), ctypes.byref(intr), _pose_arg(T_world_lidar),
                                  _stream(stream)), "integrate_lidar")
 
 
@@ -214,7 +234,7 @@ def integrate_color(m: int, depth, rgba, intr: Pinhole, T_world_cam, stream=None
     """depth: float32 [H, W] device tensor; rgba: uint32 (int32) [H, W] device
     tensor, r in the low byte."""
     _check(lib().integrate_color(m, _dptr(depth), _dptr(rgba), ctypes.byref(intr),
-                                 _pose(T_world_cam), _stream(stream)), "integrate_color")
+                                 _pose_arg(T_world_cam), _stream(stream)), "integrate_color")
 
 
 def integrate_batch(maps, frames, stream=None):
@@ -388,7 +408,7 @@ def integrate_depth_static(buffers: MapBuffers, voxel_size: float, truncation_vo
     storage; raises TsdfError with the C status on failure."""
     _check(lib().integrate_depth_static(ctypes.byref(buffers), voxel_size, truncation_voxels,
                                         max_weight, _dptr(depth), ctypes.byref(intr),
-                                        _pose(T_world_cam), _stream(stream)),
+                                        _pose_arg(T_world_cam), _stream(stream)),
            "integrate_depth_static")
 
 

@@ -263,12 +263,14 @@ tsdf_status integrate_one(tsdf_map* m, int kind, const tsdf_pinhole* ph, const t
   cudaEvent_t* ev = timing_slot(m);
   if (ev) cudaEventRecord(ev[0], s);
   const int th = m->tile_h ? m->tile_h : pick_tile_h((int64_t)p.fr[0].width * p.fr[0].height);
-  if (gbt::launch_band_alloc(p, alloc_ctas(p.fr[0], th), th, s) != cudaSuccess) return cuda_fail();
+  // one frame per call: each launch may be scheduled while the stream's
+  // previous kernel finishes (both kernels wait for it before touching memory)
+  if (gbt::launch_band_alloc(p, alloc_ctas(p.fr[0], th), th, s, true) != cudaSuccess) return cuda_fail();
   if (ev) {
     cudaEventRecord(ev[1], s);
     cudaEventRecord(ev[2], s);
   }
-  if (gbt::launch_integrate(p, m->n_ctas_integrate, s) != cudaSuccess) return cuda_fail();
+  if (gbt::launch_integrate(p, m->n_ctas_integrate, s, true) != cudaSuccess) return cuda_fail();
   if (ev) cudaEventRecord(ev[3], s);
   m->frames += 1;
   return TSDF_OK;
