@@ -560,16 +560,18 @@ tsdf_status run_batch(tsdf_map* const* maps, int32_t n_maps, std::vector<FrameDe
       p1.maps[0] = p.maps[0];
       std::memcpy(p1.fr, p.fr, sizeof(p.fr));
     }
-    if ((n_maps == 1 ? gbt::launch_band_alloc(p1, ctas, th, sa) : gbt::launch_band_alloc(p, ctas, th, sa)) !=
-        cudaSuccess)
+    // a single sub-batch runs both kernels back to back on one stream: each
+    // may be scheduled while its predecessor drains (see integrate_one)
+    if ((n_maps == 1 ? gbt::launch_band_alloc(p1, ctas, th, sa, !piped)
+                     : gbt::launch_band_alloc(p, ctas, th, sa, !piped)) != cudaSuccess)
       return cuda_fail();
     if (ev) cudaEventRecord(ev[1], sa);
     if (piped && (cudaEventRecord(lead->ev_alloc[b & 3], sa) != cudaSuccess ||
                   cudaStreamWaitEvent(s, lead->ev_alloc[b & 3], 0) != cudaSuccess))
       return cuda_fail();
     if (ev) cudaEventRecord(ev[2], s);
-    if ((n_maps == 1 ? gbt::launch_integrate(p1, lead->n_ctas_integrate, s)
-                     : gbt::launch_integrate(p, lead->n_ctas_integrate, s)) != cudaSuccess)
+    if ((n_maps == 1 ? gbt::launch_integrate(p1, lead->n_ctas_integrate, s, !piped)
+                     : gbt::launch_integrate(p, lead->n_ctas_integrate, s, !piped)) != cudaSuccess)
       return cuda_fail();
     if (ev) cudaEventRecord(ev[3], s);
     if (piped && cudaEventRecord(lead->ev_int[b & 3], s) != cudaSuccess) return cuda_fail();
