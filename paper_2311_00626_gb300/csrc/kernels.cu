@@ -29,11 +29,12 @@
 namespace gbt {
 namespace {
 
-// Programmatic dependent launch: a kernel launched with overlap_prev may be
-// scheduled while the stream's previous kernel is still running; it waits
-// here, before its first memory access, until that kernel has completed and
-// its writes are visible (a no-op for an ordinary launch).  A kernel lets
-// the next one be scheduled once its CTAs have done their main work.
+// Programmatic dependent launch: a kernel launched with BatchParams::overlap
+// may be scheduled while the stream's previous kernel is still running; it
+// waits here, before its first memory access, until that kernel has
+// completed and its writes are visible.  Such a kernel lets the next one be
+// scheduled once its CTAs have done their main work.  Ordinary launches skip
+// both instructions.
 __device__ __forceinline__ void wait_prev_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
@@ -228,7 +229,7 @@ template <int NF, int NM, int TH, bool PINHOLE_ONLY, bool STATS>
 __global__ void __launch_bounds__(kAllocThreads)
     band_alloc_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
   constexpr int kRows = TH * kTileW / kAllocThreads;  // pixel rows per thread
-  wait_prev_grid();
+  if (p.overlap) wait_prev_grid();
   uint32_t segs = 0, cells = 0;                        // walk statistics
   __shared__ uint32_t s_set[kSetSize];
   __shared__ uint32_t s_keys[kSetSize];
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(kAllocThreads)
       }
     }
   }
-  allow_next_grid();
+  if (p.overlap) allow_next_grid();
   __syncthreads();
   // compact the tile's distinct blocks, then claim them one per thread
   for (int i = threadIdx.x; i < kSetSize; i += kAllocThreads) {
@@ -712,7 +713,7 @@ __global__ void __launch_bounds__(kIntegrateThreads)
   __shared__ unsigned long long s_pairs[NM];
   __shared__ uint32_t s_next[2];
   __shared__ FrameProj s_fp[NF];
-  wait_prev_grid();
+  if (p.overlap) wait_prev_grid();
   const int t = threadIdx.x;
   if (t < NM) s_upd[t] = s_pairs[t] = 0ull;
   for (int f = t; f < p.n_frames; f += kIntegrateThreads)
@@ -805,7 +806,7 @@ __global__ void __launch_bounds__(kIntegrateThreads)
       if (m.dirty && val != -1) m.dirty[pool] = kDirtyEsdf | kDirtyMesh;
     }
   }
-  allow_next_grid();
+  if (p.overlap) allow_next_grid();
   __syncthreads();
   if (t < p.n_maps && s_upd[t]) atomicAdd(p.maps[t].counters + kCntUpdates, s_upd[t]);
   if (t < p.n_maps && s_pairs[t]) atomicAdd(p.maps[t].counters + kCntPairs, s_pairs[t]);
@@ -927,9 +928,9 @@ bool pinhole_only(const BatchParams<NF, NM>& p) {
   return true;
 }
 
-// Launch kernel k; with overlap_prev as a programmatic dependent launch.
+// Launch kernel k; with p.overlap as a programmatic dependent launch.
 template <class P>
-cudaError_t launch_k(void (*k)(P), dim3 g, dim3 b, cudaStream_t s, bool overlap_prev, const P& p) {
+cudaError_t launch_k(void (*k)(P), dim3 g, dim3 b, cudaStream_t s, const P& p) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = g;
   cfg.blockDim = b;
@@ -938,14 +939,13 @@ cudaError_t launch_k(void (*k)(P), dim3 g, dim3 b, cudaStream_t s, bool overlap_
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = overlap_prev ? at : nullptr;
-  cfg.numAttrs = overlap_prev ? 1 : 0;
+  cfg.attrs = p.overlap ? at : nullptr;
+  cfg.numAttrs = p.overlap ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, k, p);
 }
 
 template <int NF, int NM>
-cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile_h, cudaStream_t s,
-                              bool overlap_prev) {
+cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile_h, cudaStream_t s) {
   if (n_ctas <= 0) return cudaSuccess;
   const bool ph = pinhole_only(p);
   bool st = false;
@@ -953,22 +953,22 @@ cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile
   const dim3 g(n_ctas), b(kAllocThreads);
   if (st) {  // diagnostics: one generic variant per tile height
     if (tile_h == kTileHBig)
-      return launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, true>, g, b, s, overlap_prev, p);
+      return launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, true>, g, b, s, p);
     else
-      return launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, true>, g, b, s, overlap_prev, p);
+      return launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, true>, g, b, s, p);
   } else if (tile_h == kTileHBig && ph) {
-    return launch_k(band_alloc_kernel<NF, NM, kTileHBig, true, false>, g, b, s, overlap_prev, p);
+    return launch_k(band_alloc_kernel<NF, NM, kTileHBig, true, false>, g, b, s, p);
   } else if (tile_h == kTileHBig) {
-    return launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, false>, g, b, s, overlap_prev, p);
+    return launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, false>, g, b, s, p);
   } else if (ph) {
-    return launch_k(band_alloc_kernel<NF, NM, kTileHSmall, true, false>, g, b, s, overlap_prev, p);
+    return launch_k(band_alloc_kernel<NF, NM, kTileHSmall, true, false>, g, b, s, p);
   } else {
-    return launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, false>, g, b, s, overlap_prev, p);
+    return launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, false>, g, b, s, p);
   }
 }
 
 template <int NF, int NM>
-cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStream_t s, bool overlap_prev) {
+cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStream_t s) {
   // all maps of a batch share one storage type (checked by the host API)
   // colour maps take pinhole frames only (checked by the host API)
   const bool ph = pinhole_only(p);
@@ -979,35 +979,34 @@ cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStrea
   for (int k = 0; k < p.n_maps; ++k) wt = wt || p.maps[k].weighting != 0;
   const dim3 g(n_ctas), b(kIntegrateThreads);
   if (st == kStorageColor)
-    return launch_k(integrate_kernel<NF, NM, kStorageColor, true, false>, g, b, s, overlap_prev, p);
+    return launch_k(integrate_kernel<NF, NM, kStorageColor, true, false>, g, b, s, p);
   else if (st == kStorageOcc && ph)
-    return launch_k(integrate_kernel<NF, NM, kStorageOcc, true, false>, g, b, s, overlap_prev, p);
+    return launch_k(integrate_kernel<NF, NM, kStorageOcc, true, false>, g, b, s, p);
   else if (st == kStorageOcc)
-    return launch_k(integrate_kernel<NF, NM, kStorageOcc, false, false>, g, b, s, overlap_prev, p);
+    return launch_k(integrate_kernel<NF, NM, kStorageOcc, false, false>, g, b, s, p);
   else if (st == kStorageF16 && wt)
-    return launch_k(integrate_kernel<NF, NM, kStorageF16, false, true>, g, b, s, overlap_prev, p);
+    return launch_k(integrate_kernel<NF, NM, kStorageF16, false, true>, g, b, s, p);
   else if (st == kStorageF16 && ph)
-    return launch_k(integrate_kernel<NF, NM, kStorageF16, true, false>, g, b, s, overlap_prev, p);
+    return launch_k(integrate_kernel<NF, NM, kStorageF16, true, false>, g, b, s, p);
   else if (st == kStorageF16)
-    return launch_k(integrate_kernel<NF, NM, kStorageF16, false, false>, g, b, s, overlap_prev, p);
+    return launch_k(integrate_kernel<NF, NM, kStorageF16, false, false>, g, b, s, p);
   else if (wt)
-    return launch_k(integrate_kernel<NF, NM, kStorageF32, false, true>, g, b, s, overlap_prev, p);
+    return launch_k(integrate_kernel<NF, NM, kStorageF32, false, true>, g, b, s, p);
   else if (ph)
-    return launch_k(integrate_kernel<NF, NM, kStorageF32, true, false>, g, b, s, overlap_prev, p);
+    return launch_k(integrate_kernel<NF, NM, kStorageF32, true, false>, g, b, s, p);
   else
-    return launch_k(integrate_kernel<NF, NM, kStorageF32, false, false>, g, b, s, overlap_prev, p);
+    return launch_k(integrate_kernel<NF, NM, kStorageF32, false, false>, g, b, s, p);
 }
 
-template cudaError_t launch_band_alloc<1, 1>(const BatchParams<1, 1>&, int, int, cudaStream_t, bool);
+template cudaError_t launch_band_alloc<1, 1>(const BatchParams<1, 1>&, int, int, cudaStream_t);
 template cudaError_t launch_band_alloc<kMaxFrames, kMaxMaps>(const BatchParams<kMaxFrames, kMaxMaps>&,
-                                                             int, int, cudaStream_t, bool);
-template cudaError_t launch_integrate<1, 1>(const BatchParams<1, 1>&, int, cudaStream_t, bool);
+                                                             int, int, cudaStream_t);
+template cudaError_t launch_integrate<1, 1>(const BatchParams<1, 1>&, int, cudaStream_t);
 template cudaError_t launch_band_alloc<kMaxFrames, 1>(const BatchParams<kMaxFrames, 1>&, int, int,
-                                                     cudaStream_t, bool);
-template cudaError_t launch_integrate<kMaxFrames, 1>(const BatchParams<kMaxFrames, 1>&, int, cudaStream_t,
-                                                    bool);
+                                                     cudaStream_t);
+template cudaError_t launch_integrate<kMaxFrames, 1>(const BatchParams<kMaxFrames, 1>&, int, cudaStream_t);
 template cudaError_t launch_integrate<kMaxFrames, kMaxMaps>(const BatchParams<kMaxFrames, kMaxMaps>&,
-                                                            int, cudaStream_t, bool);
+                                                            int, cudaStream_t);
 
 cudaError_t launch_query(const MapDev& m, const float* pts, int64_t n, float* dist, float* weight,
                          cudaStream_t s) {

@@ -265,12 +265,13 @@ tsdf_status integrate_one(tsdf_map* m, int kind, const tsdf_pinhole* ph, const t
   const int th = m->tile_h ? m->tile_h : pick_tile_h((int64_t)p.fr[0].width * p.fr[0].height);
   // one frame per call: each launch may be scheduled while the stream's
   // previous kernel finishes (both kernels wait for it before touching memory)
-  if (gbt::launch_band_alloc(p, alloc_ctas(p.fr[0], th), th, s, true) != cudaSuccess) return cuda_fail();
+  p.overlap = 1;
+  if (gbt::launch_band_alloc(p, alloc_ctas(p.fr[0], th), th, s) != cudaSuccess) return cuda_fail();
   if (ev) {
     cudaEventRecord(ev[1], s);
     cudaEventRecord(ev[2], s);
   }
-  if (gbt::launch_integrate(p, m->n_ctas_integrate, s, true) != cudaSuccess) return cuda_fail();
+  if (gbt::launch_integrate(p, m->n_ctas_integrate, s) != cudaSuccess) return cuda_fail();
   if (ev) cudaEventRecord(ev[3], s);
   m->frames += 1;
   return TSDF_OK;
@@ -562,16 +563,17 @@ tsdf_status run_batch(tsdf_map* const* maps, int32_t n_maps, std::vector<FrameDe
     }
     // a single sub-batch runs both kernels back to back on one stream: each
     // may be scheduled while its predecessor drains (see integrate_one)
-    if ((n_maps == 1 ? gbt::launch_band_alloc(p1, ctas, th, sa, !piped)
-                     : gbt::launch_band_alloc(p, ctas, th, sa, !piped)) != cudaSuccess)
+    p.overlap = p1.overlap = piped ? 0 : 1;
+    if ((n_maps == 1 ? gbt::launch_band_alloc(p1, ctas, th, sa) : gbt::launch_band_alloc(p, ctas, th, sa)) !=
+        cudaSuccess)
       return cuda_fail();
     if (ev) cudaEventRecord(ev[1], sa);
     if (piped && (cudaEventRecord(lead->ev_alloc[b & 3], sa) != cudaSuccess ||
                   cudaStreamWaitEvent(s, lead->ev_alloc[b & 3], 0) != cudaSuccess))
       return cuda_fail();
     if (ev) cudaEventRecord(ev[2], s);
-    if ((n_maps == 1 ? gbt::launch_integrate(p1, lead->n_ctas_integrate, s, !piped)
-                     : gbt::launch_integrate(p, lead->n_ctas_integrate, s, !piped)) != cudaSuccess)
+    if ((n_maps == 1 ? gbt::launch_integrate(p1, lead->n_ctas_integrate, s)
+                     : gbt::launch_integrate(p, lead->n_ctas_integrate, s)) != cudaSuccess)
       return cuda_fail();
     if (ev) cudaEventRecord(ev[3], s);
     if (piped && cudaEventRecord(lead->ev_int[b & 3], s) != cudaSuccess) return cuda_fail();

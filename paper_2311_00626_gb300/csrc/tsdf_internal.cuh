@@ -130,6 +130,7 @@ template <int NF, int NM>
 struct BatchParams {
   int32_t n_frames;
   int32_t n_maps;
+  int32_t overlap;  // launched as a programmatic dependent of the stream's previous kernel
   MapDev maps[NM];
   FrameDev fr[NF];
 };
@@ -170,11 +171,9 @@ __device__ __forceinline__ int hash_find(const MapDev& m, unsigned long long key
 }
 
 template <int NF, int NM>
-cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile_h, cudaStream_t s,
-                              bool overlap_prev = false);
+cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile_h, cudaStream_t s);
 template <int NF, int NM>
-cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStream_t s,
-                             bool overlap_prev = false);
+cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStream_t s);
 cudaError_t launch_query_color(const MapDev& m, const float* pts, int64_t n, float* rgb, float* weight,
                                cudaStream_t s);
 cudaError_t launch_query(const MapDev& m, const float* pts, int64_t n, float* dist, float* weight,
