@@ -59,3 +59,17 @@ def test_header_compiles_as_c_and_layouts_agree(tmp_path):
     assert vals == [ctypes.sizeof(gt.Pinhole), ctypes.sizeof(gt.Lidar), ctypes.sizeof(gt.MapOpts),
                     ctypes.sizeof(gt.FrameDesc), gt.FrameDesc.depth_dev.offset,
                     gt.FrameDesc.color_dev.offset, ctypes.sizeof(gt.EsdfOpts)]
+
+
+def test_pose_argument_marshalling():
+    """Poses reach the C calls as 16 row-major doubles: a contiguous float64
+    array is passed as its own memory, anything else as a copy with the
+    same values."""
+    import numpy as np
+    T = np.arange(16, dtype=np.float64).reshape(4, 4)
+    assert gt._pose_arg(T) == T.ctypes.data
+    for other in (T.tolist(), T.astype(np.float32), np.asfortranarray(T), T[:, :]):
+        arg = gt._pose_arg(other)
+        vals = list(arg) if not isinstance(arg, int) else \
+            list((ctypes.c_double * 16).from_address(arg))
+        assert vals == T.reshape(16).tolist()
