@@ -77,19 +77,6 @@ __device__ __forceinline__ void add_update(const EsdfDev& e, uint32_t* list, uin
   if (atomicExch(e.stamp_s + p, gen) != gen) list[atomicAdd(size, 1u)] = p;
 }
 
-// TSDF value of voxel l of pool block p (FP32 storage {D, W}; FP16 {D/tau, W}).
-__device__ __forceinline__ void tsdf_at(const MapDev& m, uint32_t p, int l, float& D, float& W) {
-  if (m.storage == kStorageF16) {
-    const __half2 h = reinterpret_cast<const __half2*>(m.pool)[(size_t)p * 512 + l];
-    D = __low2float(h) * m.tau;
-    W = __high2float(h);
-  } else {
-    const float2 v = reinterpret_cast<const float2*>(m.pool)[(size_t)p * 512 + l];
-    D = v.x;
-    W = v.y;
-  }
-}
-
 // Hashed bitmaps of the blocks where a site disappeared (lost-site blocks)
 // and of their coarse cells (cubes of G = R + 1 blocks, R the reach of a
 // parent in blocks), written by the mark stage for the clear stage.
@@ -108,42 +95,64 @@ __device__ __forceinline__ bool bit_set(const uint32_t* bits, uint32_t b) {
 
 // ------------------------------------------------------------- mark sites
 
+// One warp per pool block, 16 voxels per lane (voxels 128 j + 4 lane + i),
+// read and written as 16-byte vectors.
 __global__ void __launch_bounds__(kEsdfThreads)
     esdf_mark_kernel(const MapDev m, const EsdfDev e, uint32_t gen) {
+  constexpr int kWarps = kEsdfThreads / 32;
   const uint32_t nb = n_blocks(m);
-  const int t = threadIdx.x;
-  for (uint32_t p = blockIdx.x; p < nb; p += gridDim.x) {
-    if (!(m.dirty[p] & kDirtyEsdf)) continue;  // same value for every thread of the CTA
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (uint32_t p = blockIdx.x * kWarps + warp; p < nb; p += gridDim.x * kWarps) {
+    if (!(m.dirty[p] & kDirtyEsdf)) continue;  // same value for every lane
+    uint4* stb = reinterpret_cast<uint4*>(e.st + (size_t)p * 512) + lane;
     bool any = false, lost = false;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int l = 4 * t + i;
-      float D, W;
-      tsdf_at(m, p, l, D, W);
-      const bool obs = W >= e.min_weight;
-      const bool site = obs && fabsf(D) <= e.site_eps;
-      const bool inside = obs && D < 0.0f;
-      uint32_t* sp = e.st + (size_t)p * 512 + l;
-      const uint32_t old = *sp;
-      uint32_t s = old;
-      if (site) {
-        s = kEsdfObs | kEsdfSite | kEsdfPar | (inside ? kEsdfInside : 0u);
-      } else if (old & kEsdfSite) {
-        s = obs ? (kEsdfObs | (inside ? kEsdfInside : 0u)) : 0u;
-        lost = true;
-      } else if (!obs) {
-        s = 0u;
-      } else if (!(old & kEsdfObs) || ((old & kEsdfInside) != 0u) != inside) {
-        s = kEsdfObs | (inside ? kEsdfInside : 0u);
+    for (int j = 0; j < 4; ++j) {
+      float D[4], W[4];
+      if (m.storage == kStorageF16) {
+        const uint4 raw = reinterpret_cast<const uint4*>(m.pool)[(size_t)p * 128 + 32 * j + lane];
+        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const __half2 h = *reinterpret_cast<const __half2*>(&w4[i]);
+          D[i] = __low2float(h) * m.tau;
+          W[i] = __high2float(h);
+        }
+      } else {
+        const float4* src = reinterpret_cast<const float4*>(m.pool) + (size_t)p * 256 + 64 * j + 2 * lane;
+        const float4 a = src[0], b = src[1];
+        D[0] = a.x; W[0] = a.y; D[1] = a.z; W[1] = a.w;
+        D[2] = b.x; W[2] = b.y; D[3] = b.z; W[3] = b.w;
       }
-      if (s != old) {
-        *sp = s;
-        any = true;
+      const uint4 o4 = stb[32 * j];
+      const uint32_t old[4] = {o4.x, o4.y, o4.z, o4.w};
+      uint32_t nw[4];
+      bool changed = false;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const bool obs = W[i] >= e.min_weight;
+        const bool site = obs && fabsf(D[i]) <= e.site_eps;
+        const bool inside = obs && D[i] < 0.0f;
+        uint32_t s = old[i];
+        if (site) {
+          s = kEsdfObs | kEsdfSite | kEsdfPar | (inside ? kEsdfInside : 0u);
+        } else if (old[i] & kEsdfSite) {
+          s = obs ? (kEsdfObs | (inside ? kEsdfInside : 0u)) : 0u;
+          lost = true;
+        } else if (!obs) {
+          s = 0u;
+        } else if (!(old[i] & kEsdfObs) || ((old[i] & kEsdfInside) != 0u) != inside) {
+          s = kEsdfObs | (inside ? kEsdfInside : 0u);
+        }
+        nw[i] = s;
+        changed = changed || s != old[i];
       }
+      if (changed) stb[32 * j] = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+      any = any || changed;
     }
-    any = __syncthreads_or(any);   // also: every thread has read dirty[p]
-    lost = __syncthreads_or(lost);
-    if (t == 0) {
+    any = __any_sync(0xffffffffu, any);  // also: every lane has read dirty[p]
+    lost = __any_sync(0xffffffffu, lost);
+    if (lane == 0) {
       m.dirty[p] &= (uint8_t)~kDirtyEsdf;
       if (any) add_update(e, e.list[0], e.cnt, p, gen);
       if (lost) {
@@ -498,7 +507,7 @@ int grid_for(int per_sm) {
 }  // namespace
 
 cudaError_t launch_esdf_mark(const MapDev& m, const EsdfDev& e, uint32_t gen, cudaStream_t s) {
-  esdf_mark_kernel<<<grid_for(8), kEsdfThreads, 0, s>>>(m, e, gen);
+  esdf_mark_kernel<<<grid_for(16), kEsdfThreads, 0, s>>>(m, e, gen);
   return cudaGetLastError();
 }
 
