@@ -33,7 +33,7 @@
 namespace gbt {
 namespace {
 
-constexpr int kEsdfThreads = 128;  // 4 voxels per thread
+constexpr int kEsdfThreads = 128;  // threads per CTA (4 voxels each, or 4 warps of 16)
 
 __device__ __forceinline__ int off_comp(uint32_t s, int axis) {
   const int raw = (int)((s >> (9 * axis)) & 511u);
@@ -395,21 +395,28 @@ __global__ void __launch_bounds__(kEsdfThreads)
   }
 }
 
-// Copy the changed blocks back; they form the next update set.
-// Thread 0 of CTA 0 zeroes the other tlist's size (used by the previous
-// iteration, filled by the next one).
+// Copy the changed blocks back; they form the next update set.  One warp
+// per tlist entry, four 16-byte vectors per lane.  Thread 0 of CTA 0 zeroes
+// the other tlist's size (used by the previous iteration, filled by the
+// next one).
 __global__ void __launch_bounds__(kEsdfThreads)
     esdf_apply_kernel(const EsdfDev e, const uint32_t* __restrict__ tlist, const uint32_t* tsize,
                       uint32_t* zero_tsize, uint32_t* next, uint32_t* next_size, uint32_t gen_next) {
+  constexpr int kWarps = kEsdfThreads / 32;
   const uint32_t n = __ldcg(tsize);
-  const int t = threadIdx.x;
-  if (blockIdx.x == 0 && t == 0) *zero_tsize = 0u;
-  for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *zero_tsize = 0u;
+  for (uint32_t k = blockIdx.x * kWarps + warp; k < n; k += gridDim.x * kWarps) {
     if (!e.tchanged[k]) continue;
     const uint32_t p = tlist[k];
-    reinterpret_cast<uint4*>(e.st + (size_t)p * 512)[t] =
-        reinterpret_cast<const uint4*>(e.st2 + (size_t)p * 512)[t];
-    if (t == 0) add_update(e, next, next_size, p, gen_next);
+    uint4* dst = reinterpret_cast<uint4*>(e.st + (size_t)p * 512) + lane;
+    const uint4* src = reinterpret_cast<const uint4*>(e.st2 + (size_t)p * 512) + lane;
+    uint4 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = src[32 * j];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dst[32 * j] = v[j];
+    if (lane == 0) add_update(e, next, next_size, p, gen_next);
   }
 }
 
