@@ -222,6 +222,20 @@ tsdf_status integrate_batch_host(tsdf_map* const* maps, int32_t n_maps, const ts
                                  int32_t n, void* staging_dev, int64_t staging_bytes, void* cuda_stream);
 
 /*
+ * stage_frames — enqueue n host-to-device copies on cuda_stream: bytes[i]
+ * bytes from host src_host[i] (pinned for the copy to be asynchronous) to
+ * device dst_dev[i].  A staging helper for callers that place images
+ * themselves (a serving loop with its own device ring), one call per batch
+ * instead of one per image.  The three arrays are host memory read during
+ * the call; the images must stay valid, and the destinations unused, until
+ * the stream passes the copies.  TSDF_ERR_ARG for n < 0, a null array, a
+ * null pointer or a negative size (nothing is enqueued then); a failed copy
+ * returns TSDF_ERR_CUDA after the copies before it were enqueued.
+ */
+tsdf_status stage_frames(const void* const* src_host, void* const* dst_dev, const int64_t* bytes, int32_t n,
+                         void* cuda_stream);
+
+/*
  * query_voxels — TSDF value at n points (float32 [n][3], layer frame,
  * metres): the voxel containing each point, looked up in the block hash.
  * Writes dist_dev[n] and weight_dev[n]; unallocated or unobserved voxels

@@ -41,7 +41,7 @@ EXPORTED_SYMBOLS = ["map_create", "map_create_ex", "integrate_depth", "integrate
                     "integrate_depth_static", "integrate_color", "query_color",
                     "map_export_color", "map_decay_occupancy", "map_import", "map_esdf_update",
                     "map_esdf_export", "map_esdf_query", "map_esdf_stats", "map_walk_stats",
-                    "map_mesh", "integrate_batch_host"]
+                    "map_mesh", "integrate_batch_host", "stage_frames"]
 
 
 class TsdfError(RuntimeError):
@@ -112,6 +112,7 @@ def lib():
                 "integrate_lidar": ([P, P, ctypes.POINTER(Lidar), P, P], I),
                 "integrate_batch": ([P, I, ctypes.POINTER(FrameDesc), I, P], I),
                 "integrate_batch_host": ([P, I, ctypes.POINTER(FrameDesc), I, P, L64, P], I),
+                "stage_frames": ([P, P, P, I, P], I),
                 "query_voxels": ([P, P, L64, P, P, P], I),
                 "map_sync": ([P], I),
                 "map_num_blocks": ([P, ctypes.POINTER(ctypes.c_int64)], I),
@@ -254,6 +255,18 @@ def integrate_batch_host(maps, frames, staging, stream=None):
     nbytes = staging.numel() * staging.element_size()
     _check(lib().integrate_batch_host(arr_m, len(maps), arr_f, len(frames), staging.data_ptr(), nbytes,
                                       _stream(stream)), "integrate_batch_host")
+
+
+def stage_frames(src_host, dst_dev, nbytes, stream=None):
+    """Enqueue host-to-device copies src_host[i] -> dst_dev[i] of nbytes[i]
+    bytes (pointers as ints) on `stream` in one C call."""
+    n = len(src_host)
+    if not (len(dst_dev) == len(nbytes) == n):
+        raise ValueError("stage_frames: arrays of different lengths")
+    src = (ctypes.c_void_p * n)(*src_host)
+    dst = (ctypes.c_void_p * n)(*dst_dev)
+    cnt = (ctypes.c_int64 * n)(*nbytes)
+    _check(lib().stage_frames(src, dst, cnt, n, _stream(stream)), "stage_frames")
 
 
 def query_voxels(m: int, pts, dist, weight, stream=None):
@@ -519,6 +532,9 @@ def frame_desc(map_index: int, sensor: dict, T, depth, rgba=None) -> FrameDesc:
         fd.kind = SENSOR_LIDAR
         fd.lidar = lidar(sensor)
     fd.depth_dev = _dptr(depth)
-    fd.T_world_sensor = _pose(T)
+    if type(T) is np.ndarray and T.dtype == np.float64 and T.size == 16 and T.flags.c_contiguous:
+        ctypes.memmove(ctypes.addressof(fd) + FrameDesc.T_world_sensor.offset, T.ctypes.data, 128)
+    else:
+        fd.T_world_sensor = _pose(T)
     fd.color_dev = _dptr(rgba) if rgba is not None else None
     return fd

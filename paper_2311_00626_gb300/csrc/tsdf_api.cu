@@ -695,6 +695,19 @@ tsdf_status integrate_batch_host(tsdf_map* const* maps, int32_t n_maps, const ts
   return TSDF_OK;
 }
 
+tsdf_status stage_frames(const void* const* src_host, void* const* dst_dev, const int64_t* bytes, int32_t n,
+                         void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!src_host || !dst_dev || !bytes))) return TSDF_ERR_ARG;
+  for (int32_t i = 0; i < n; ++i)
+    if (!src_host[i] || !dst_dev[i] || bytes[i] < 0) return TSDF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  for (int32_t i = 0; i < n; ++i)
+    if (bytes[i] > 0 &&
+        cudaMemcpyAsync(dst_dev[i], src_host[i], (size_t)bytes[i], cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return cuda_fail();
+  return TSDF_OK;
+}
+
 tsdf_status query_voxels(const tsdf_map* map, const float* pts_dev, int64_t n, float* dist_dev,
                          float* weight_dev, void* cuda_stream) {
   if (!map || n < 0 || (n > 0 && (!pts_dev || !dist_dev || !weight_dev))) return TSDF_ERR_ARG;

@@ -9,8 +9,9 @@ up to 32 frames over up to 16 maps.  It is continuous batching:
   free slot (frames per launch) and the device staging ring has room for the
   request's depth image (admission by HBM footprint); the rest wait;
 - the admitted frames are copied from pinned host memory on a copy stream
-  while the previous batch is still integrating on the compute stream, so a
-  batch's copies overlap the GPU work of the one before it;
+  (one `stage_frames` call per batch) while the previous batch is still
+  integrating on the compute stream, so a batch's copies overlap the GPU
+  work of the one before it;
 - a batch launches as soon as its copies are enqueued; its staging bytes are
   released when its completion event has fired;
 - per-request latency is completion minus arrival (host clock), reported as
@@ -30,7 +31,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import FrameDesc, TsdfMap, frame_desc, integrate_batch
+from . import FrameDesc, TsdfMap, frame_desc, integrate_batch, stage_frames
 
 MAX_FRAMES = 32
 MAX_MAPS = 16
@@ -57,6 +58,7 @@ class StagingRing:
 
     def __init__(self, torch, nbytes: int, device):
         self.buf = torch.empty(nbytes // 4, dtype=torch.float32, device=device)
+        self.base = self.buf.data_ptr()
         self.cap = nbytes
         self.head = 0      # next free byte
         self.used = 0
@@ -145,11 +147,11 @@ class Server:
 
     def _launch(self, batch, slices):
         torch = self.torch
-        with torch.cuda.stream(self.copy_stream):
-            for r in batch:
-                dst = self.ring.view(r._slot[0], r.depth.numel())
-                dst.copy_(r.depth.view(-1), non_blocking=True)
-                r._dev = dst
+        # the batch's images into their ring slices: one library call
+        for r in batch:
+            r._dev = self.ring.base + r._slot[0]
+        stage_frames([r.depth.data_ptr() for r in batch], [r._dev for r in batch],
+                     [r.nbytes for r in batch], self.copy_stream)
         copied = torch.cuda.Event()
         copied.record(self.copy_stream)
         self.compute_stream.wait_event(copied)

@@ -92,3 +92,27 @@ def test_host_batch_staging_too_small(room):
     torch.cuda.synchronize()
     assert m.num_blocks() == 0
     m.close()
+
+
+def test_stage_frames_copies_and_refuses_bad_arguments():
+    """stage_frames enqueues each host image into its device slice (sizes
+    from zero to a full 1280x720 image, slices out of order), and refuses
+    null pointers and negative sizes before enqueuing anything."""
+    rng = np.random.default_rng(7)
+    sizes = [0, 4, 1000, 640 * 480, 1280 * 720, 37]
+    host = [torch.from_numpy(rng.standard_normal(max(n, 1)).astype(np.float32)).pin_memory() for n in sizes]
+    offs = np.cumsum([0] + [(max(n, 1) * 4 + 255) // 256 * 256 for n in sizes])
+    dev = torch.zeros(int(offs[-1]) // 4, dtype=torch.float32, device="cuda")
+    order = [3, 0, 5, 1, 4, 2]
+    gt.stage_frames([host[i].data_ptr() for i in order], [dev.data_ptr() + int(offs[i]) for i in order],
+                    [sizes[i] * 4 for i in order])
+    torch.cuda.synchronize()
+    for i, n in enumerate(sizes):
+        got = dev[int(offs[i]) // 4: int(offs[i]) // 4 + n].cpu().numpy()
+        np.testing.assert_array_equal(got, host[i][:n].numpy())
+    assert float(dev[int(offs[0]) // 4]) == 0.0  # the zero-byte entry wrote nothing
+    with pytest.raises(gt.TsdfError):
+        gt.stage_frames([host[1].data_ptr(), 0], [dev.data_ptr(), dev.data_ptr()], [16, 16])
+    with pytest.raises(gt.TsdfError):
+        gt.stage_frames([host[1].data_ptr()], [dev.data_ptr()], [-4])
+    gt.stage_frames([], [], [])  # nothing to do
