@@ -103,7 +103,7 @@ class Server:
     """Continuous-batching integration server over device-resident maps."""
 
     def __init__(self, maps: list, staging_bytes: int = 256 << 20, max_frames: int = MAX_FRAMES,
-                 max_in_flight: int = 2):
+                 max_in_flight: int = 4):
         import torch
         self.torch = torch
         self.maps = maps
