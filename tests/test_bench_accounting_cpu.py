@@ -32,3 +32,12 @@ def test_mesh_bytes():
     assert bench.mesh_bytes(1, 0) == 4096
     assert bench.mesh_bytes(0, 1) == 36
     assert bench.mesh_bytes(20369, 1168505) == 20369 * 4096 + 1168505 * 36
+
+
+def test_alu_operation_counts_match_their_itemisation():
+    """The ALU rooflines' algorithmic operation counts are the sums of the
+    items listed beside them in bench.py."""
+    segment = 6 + 3 + 3 + 3 + 6 + 3 * (2 + 1 + 1 + 2) + 7
+    cell = 4 + 2 + 4 + 2
+    projection = 2 + 3 + 1 + 6 + 5 + 3 + 1 + 1 + 3 + 7
+    assert (bench.OPS_PER_SEGMENT, bench.OPS_PER_CELL, bench.OPS_PER_PROJECTION) == (segment, cell, projection)
