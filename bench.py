@@ -47,7 +47,7 @@ OPS_PER_CELL = 12
 # voxel x coordinate 2, position 3, reciprocal depth 1, pixel 6, in-image 5,
 # pixel index 3, depth load 1, d_p 1, validity 3, update (clamp, weight sum,
 # difference, quotient 2, sum, cap) 7
-OPS_PER_PROJECTION = 34
+OPS_PER_PROJECTION = 32
 
 
 def _peaks():
