@@ -20,7 +20,8 @@
  *    has finished; pointers named *_host are host memory.  Poses are host
  *    memory, row-major 4x4 doubles, read during the call (copied by value).
  *  - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).
- *    Calls return as soon as their work is enqueued.
+ *    Calls return as soon as their work is enqueued, except those whose
+ *    description says they synchronise or wait.
  *  - Argument errors are returned synchronously and enqueue nothing.
  *    Errors found on the device (pool or hash full, work list full) are
  *    sticky on the map and returned by map_sync() and by every later call;
