@@ -172,6 +172,7 @@ def _stream(stream) -> int | None:
     if stream is None:
         if _torch is None:
             import torch
+            torch.cuda.init()  # the raw getter below does not initialise CUDA itself
             _torch = torch
             # the raw getter avoids building a Stream object on every call
             _raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
