@@ -37,7 +37,7 @@
  * Precision: discrete decisions (blocks met by a band segment, pixel choice,
  * sample validity, the d_p >= -tau test, LiDAR cell choice) are taken in a
  * prescribed FP32 operation sequence; values are accumulated in FP32 and
- * stored in FP32 or FP16 (D / tau and W as halves).  Poses are composed in
+ * stored in FP32, FP16 or 16-bit fixed point (TSDF_STORAGE_*).  Poses are composed in
  * FP64 on the host and passed to the GPU as FP32, relative to the block that
  * contains the sensor origin.
  */
@@ -78,7 +78,18 @@ typedef struct {
   float min_range, max_range;
 } tsdf_lidar;
 
-enum { TSDF_STORAGE_FP32 = 0, TSDF_STORAGE_FP16 = 1 };
+/* TSDF voxel storage (arithmetic is FP32 in every case).  FP32: D and W as
+ * floats, 8 B per voxel.  FP16: D / tau and W as halves, 4 B per voxel.
+ * FIXED16: D / tau as a 16-bit signed fixed-point fraction (32767 steps per
+ * tau, rounded to nearest) and W as a half, 4 B per voxel.  Both 4-byte forms
+ * hold integer weights up to 2048 exactly.  Each update rounds the stored D
+ * once, so with the running average at the weight cap (a step of
+ * (s - D) / (max_weight + 1)) the stored D can stay up to
+ * (max_weight + 1) / 2 units of its last place from the exact average: FP16
+ * units are 2^-11 tau for |D| >= tau / 2, fixed-point units a uniform
+ * tau / 32767, so FIXED16 bounds that error by (max_weight + 1) / 65534 tau
+ * (1.5e-3 tau at max_weight 100). */
+enum { TSDF_STORAGE_FP32 = 0, TSDF_STORAGE_FP16 = 1, TSDF_STORAGE_FIXED16 = 2 };
 /* Layers (Sec. IV-A: a map of co-located layers; Sec. IV-B: one update
  * functor per layer).  An occupancy layer holds one FP32 log-odds per voxel:
  * every voxel that passes the same projection test as the TSDF (d_p >= -tau)
@@ -103,7 +114,7 @@ enum { TSDF_WEIGHT_CONSTANT = 0, TSDF_WEIGHT_INV_SQUARE = 1, TSDF_WEIGHT_DROPOFF
 enum { TSDF_SENSOR_PINHOLE = 0, TSDF_SENSOR_LIDAR = 1 };
 
 /* Map options.  max_blocks: pool size in blocks (4 KiB per block in FP32,
- * 2 KiB in FP16); hash_capacity: hash slots, rounded up to a power of two,
+ * 2 KiB in FP16 or FIXED16); hash_capacity: hash slots, rounded up to a power of two,
  * at least 2 * max_blocks (0 = that minimum).  lidar_nearest != 0 samples
  * LiDAR images at the nearest beam instead of guarded bilinear;
  * lidar_guard is the bilinear foreground/background threshold in metres
@@ -325,7 +336,7 @@ tsdf_status map_decay_occupancy(tsdf_map* map, float decay_occ, float decay_free
  * occupancy map dist is the log-odds and weight_host may be NULL).  Missing
  * blocks are allocated, present ones overwritten; every written block
  * counts as changed for the next map_esdf_update.  Values are stored in the
- * map's storage (FP16 rounds D / tau and W).  Not for colour maps.
+ * map's storage (FP16 and FIXED16 round D / tau and W).  Not for colour maps.
  * Synchronises; uses temporary device memory.
  */
 tsdf_status map_import(tsdf_map* map, const int32_t* keys_host, const float* dist_host,
@@ -413,21 +424,25 @@ tsdf_status map_destroy(tsdf_map* map);
 
 /*
  * Allocation-free integration.  The paper has no counterpart: this entry
- * point exists for callers that cannot allocate GPU memory at the time they
- * integrate (their allocator belongs to another framework, they are
- * capturing a CUDA graph, or a real-time loop forbids allocation after
- * start-up).  It integrates one pinhole frame exactly like integrate_depth
- * into FP32 map storage that the caller owns, described by tsdf_map_buffers:
+ * point is for callers that cannot allocate GPU memory when they integrate,
+ * because the device allocator belongs to another framework that owns all of
+ * the GPU's memory, or because a real-time loop forbids allocation once it
+ * has started.  It integrates one pinhole frame exactly like
+ * integrate_depth into FP32 map storage that the caller owns, described by
+ * tsdf_map_buffers:
  *   keys        uint64 [hash_capacity], every byte 0xFF before first use
  *   vals        int32  [hash_capacity], every byte 0xFF before first use
  *   mask        uint32 [hash_capacity], zero before first use
  *   pool        {float D, float W} [max_blocks][512], any initial contents
  *   block_keys  uint64 [max_blocks]: key of each pool block (written)
- *   counters    uint64 [6], zero before first use: [0] blocks allocated
- *               (pool blocks 0 .. min([0], max_blocks) - 1 are in use),
- *               [1] voxel updates, [2] status bits (nonzero = capacity
- *               exceeded), [3] block visits, [4] integration launches
+ *   counters    uint64 [TSDF_NUM_COUNTERS], zero before first use:
+ *               [0] blocks allocated (pool blocks 0 .. min([0], max_blocks) - 1
+ *               are in use), [1] voxel updates, [2] status bits (nonzero =
+ *               capacity exceeded), [3] block visits, [4] integration
+ *               launches, [5] and [6] unused (left as they are), [7] (block,
+ *               frame) pairs integrated
  * hash_capacity is a power of two >= 2 * max_blocks.  A block key packs
+ * the coordinates plus TSDF_KEY_BIAS into TSDF_KEY_BITS-bit fields:
  * (x + 2^20) | (y + 2^20) << 21 | (z + 2^20) << 42.  Between calls the
  * storage must not be modified.
  *
@@ -439,9 +454,13 @@ tsdf_status map_destroy(tsdf_map* map);
  * cudaFree or allocating library routine.  Its first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.  Every call
- * shares the one array, so calls whose work overlaps on the GPU (different
- * streams or threads) race and must be serialised by the caller.
+ * shares the one array and clears its control words before use, so calls
+ * whose work overlaps on the GPU (different streams or threads) race and
+ * must be serialised by the caller.
  */
+#define TSDF_NUM_COUNTERS 8
+#define TSDF_KEY_BITS 21
+#define TSDF_KEY_BIAS (1 << 20)
 #define TSDF_STATIC_MAX_BLOCKS (1 << 16)
 
 typedef struct {

@@ -21,17 +21,19 @@ __all__ = ["TsdfError", "Pinhole", "Lidar", "MapOpts", "FrameDesc", "TsdfMap", "
            "map_create", "map_create_ex", "integrate_depth", "integrate_lidar",
            "integrate_batch", "query_voxels", "map_sync", "map_num_blocks", "map_stats",
            "map_export", "map_reset", "map_destroy", "map_timing", "map_kernel_times",
-           "MapBuffers", "integrate_depth_static", "STATIC_MAX_BLOCKS", "LAYER_TSDF",
-           "LAYER_OCCUPANCY", "LAYER_COLOR", "STORAGE_FP32", "STORAGE_FP16",
+           "MapBuffers", "integrate_depth_static", "STATIC_MAX_BLOCKS", "NUM_COUNTERS", "LAYER_TSDF",
+           "LAYER_OCCUPANCY", "LAYER_COLOR", "STORAGE_FP32", "STORAGE_FP16", "STORAGE_FIXED16",
            "integrate_color", "query_color", "map_export_color", "map_decay_occupancy",
            "EsdfOpts", "map_import", "map_esdf_update", "map_esdf_export", "map_esdf_query",
            "map_esdf_stats", "map_walk_stats", "map_mesh", "integrate_batch_host", "frame_desc_host",
            "SENSOR_PINHOLE", "SENSOR_LIDAR", "EXPORTED_SYMBOLS"]
 
-STORAGE_FP32, STORAGE_FP16 = 0, 1
+STORAGE_FP32, STORAGE_FP16, STORAGE_FIXED16 = 0, 1, 2
 LAYER_TSDF, LAYER_OCCUPANCY, LAYER_COLOR = 0, 1, 2
 WEIGHT_CONSTANT, WEIGHT_INV_SQUARE, WEIGHT_DROPOFF = 0, 1, 2
 STATIC_MAX_BLOCKS = 1 << 16  # TSDF_STATIC_MAX_BLOCKS
+NUM_COUNTERS = 8  # TSDF_NUM_COUNTERS: u64 words of a caller-owned counters buffer
+KEY_BITS, KEY_BIAS = 21, 1 << 20  # TSDF_KEY_BITS, TSDF_KEY_BIAS
 SENSOR_PINHOLE, SENSOR_LIDAR = 0, 1
 _STATUS = {0: "TSDF_OK", -1: "TSDF_ERR_ARG", -2: "TSDF_ERR_CUDA", -3: "TSDF_ERR_CAPACITY",
            -4: "TSDF_ERR_TIMEOUT", -5: "TSDF_ERR_STATE"}

@@ -118,6 +118,14 @@ __global__ void __launch_bounds__(kEsdfThreads)
           D[i] = __low2float(h) * m.tau;
           W[i] = __high2float(h);
         }
+      } else if (m.storage == kStorageX16) {
+        const uint4 raw = reinterpret_cast<const uint4*>(m.pool)[(size_t)p * 128 + 32 * j + lane];
+        const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          D[i] = x16_dist(w4[i], m.x16_unit);
+          W[i] = x16_weight(w4[i]);
+        }
       } else {
         const float4* src = reinterpret_cast<const float4*>(m.pool) + (size_t)p * 256 + 64 * j + 2 * lane;
         const float4 a = src[0], b = src[1];
@@ -496,6 +504,8 @@ __global__ void __launch_bounds__(kEsdfThreads)
         reinterpret_cast<float*>(m.pool)[(size_t)pool * 512 + l] = d;
       } else if (m.storage == kStorageF16) {
         reinterpret_cast<__half2*>(m.pool)[(size_t)pool * 512 + l] = __floats2half2_rn(d * m.inv_tau, w);
+      } else if (m.storage == kStorageX16) {
+        reinterpret_cast<uint32_t*>(m.pool)[(size_t)pool * 512 + l] = x16_pack(d, w, m.x16_scale);
       } else {
         reinterpret_cast<float2*>(m.pool)[(size_t)pool * 512 + l] = make_float2(d, w);
       }

@@ -477,6 +477,26 @@ struct Voxels4<kStorageF16> {
 };
 
 template <>
+struct Voxels4<kStorageX16> {
+  __device__ __forceinline__ static void load(const MapDev& m, int pool, int t, float* D, float* W,
+                                              float* G, float* B) {
+    const uint4 raw = reinterpret_cast<const uint4*>(m.pool)[(size_t)pool * 128 + t];
+    const uint32_t w4[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      D[i] = x16_dist(w4[i], m.x16_unit);
+      W[i] = x16_weight(w4[i]);
+    }
+  }
+  __device__ __forceinline__ static void store(const MapDev& m, int pool, int t, const float* D,
+                                               const float* W, const float* G, const float* B) {
+    reinterpret_cast<uint4*>(m.pool)[(size_t)pool * 128 + t] =
+        make_uint4(x16_pack(D[0], W[0], m.x16_scale), x16_pack(D[1], W[1], m.x16_scale),
+                   x16_pack(D[2], W[2], m.x16_scale), x16_pack(D[3], W[3], m.x16_scale));
+  }
+};
+
+template <>
 struct Voxels4<kStorageColor> {
   __device__ __forceinline__ static void load(const MapDev& m, int pool, int t, float* D, float* W,
                                               float* G, float* B) {
@@ -848,6 +868,10 @@ __global__ void query_kernel(const MapDev m, const float* __restrict__ pts, int6
           const float2 v = reinterpret_cast<const float2*>(m.pool)[(size_t)val * 512 + l];
           outD = v.x;
           outW = v.y;
+        } else if (STORAGE == kStorageX16) {
+          const uint32_t w = reinterpret_cast<const uint32_t*>(m.pool)[(size_t)val * 512 + l];
+          outD = x16_dist(w, m.x16_unit);
+          outW = x16_weight(w);
         } else {
           const __half2 h = reinterpret_cast<const __half2*>(m.pool)[(size_t)val * 512 + l];
           outD = __low2float(h) * m.tau;
@@ -984,6 +1008,12 @@ cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStrea
     return launch_k(integrate_kernel<NF, NM, kStorageOcc, true, false>, g, b, s, p);
   else if (st == kStorageOcc)
     return launch_k(integrate_kernel<NF, NM, kStorageOcc, false, false>, g, b, s, p);
+  else if (st == kStorageX16 && wt)
+    return launch_k(integrate_kernel<NF, NM, kStorageX16, false, true>, g, b, s, p);
+  else if (st == kStorageX16 && ph)
+    return launch_k(integrate_kernel<NF, NM, kStorageX16, true, false>, g, b, s, p);
+  else if (st == kStorageX16)
+    return launch_k(integrate_kernel<NF, NM, kStorageX16, false, false>, g, b, s, p);
   else if (st == kStorageF16 && wt)
     return launch_k(integrate_kernel<NF, NM, kStorageF16, false, true>, g, b, s, p);
   else if (st == kStorageF16 && ph)
@@ -1017,6 +1047,8 @@ cudaError_t launch_query(const MapDev& m, const float* pts, int64_t n, float* di
     query_kernel<kStorageOcc><<<blocks, threads, 0, s>>>(m, pts, n, dist, weight);
   else if (m.storage == kStorageF16)
     query_kernel<kStorageF16><<<blocks, threads, 0, s>>>(m, pts, n, dist, weight);
+  else if (m.storage == kStorageX16)
+    query_kernel<kStorageX16><<<blocks, threads, 0, s>>>(m, pts, n, dist, weight);
   else
     query_kernel<kStorageF32><<<blocks, threads, 0, s>>>(m, pts, n, dist, weight);
   return cudaGetLastError();
@@ -1067,6 +1099,10 @@ int integrate_ctas_per_sm(int storage) {
   else if (storage == kStorageOcc)
     n = std::min(occupancy(integrate_kernel<F, M, kStorageOcc, true, false>),
                  occupancy(integrate_kernel<F, M, kStorageOcc, false, false>));
+  else if (storage == kStorageX16)
+    n = std::min({occupancy(integrate_kernel<F, M, kStorageX16, true, false>),
+                  occupancy(integrate_kernel<F, M, kStorageX16, false, false>),
+                  occupancy(integrate_kernel<F, M, kStorageX16, false, true>)});
   else if (storage == kStorageF16)
     n = std::min({occupancy(integrate_kernel<F, M, kStorageF16, true, false>),
                   occupancy(integrate_kernel<F, M, kStorageF16, false, false>),

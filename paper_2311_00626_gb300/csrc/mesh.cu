@@ -66,6 +66,10 @@ __device__ __forceinline__ float staged_voxel(const MapDev& m, int q, int l, flo
     const __half2 h = reinterpret_cast<const __half2*>(m.pool)[(size_t)q * 512 + l];
     d = __low2float(h) * m.tau;
     w = __high2float(h);
+  } else if (m.storage == kStorageX16) {
+    const uint32_t word = reinterpret_cast<const uint32_t*>(m.pool)[(size_t)q * 512 + l];
+    d = x16_dist(word, m.x16_unit);
+    w = x16_weight(word);
   } else {
     const float2 v = reinterpret_cast<const float2*>(m.pool)[(size_t)q * 512 + l];
     d = v.x;

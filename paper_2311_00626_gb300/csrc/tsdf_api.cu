@@ -212,7 +212,7 @@ tsdf_status fill_frame(tsdf_map* m, int map_index, int kind, const tsdf_pinhole*
 }
 
 size_t voxel_size_bytes(int storage) {
-  return storage == gbt::kStorageColor ? 16 : storage == TSDF_STORAGE_FP32 ? 8 : 4;
+  return storage == gbt::kStorageColor ? 16 : storage == TSDF_STORAGE_FP32 ? 8 : 4;  // FP16, fixed 16, occupancy
 }
 
 int alloc_ctas(const FrameDev& F, int tile_h) {
@@ -368,7 +368,7 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   if (o.alloc_tile_h != 0 && o.alloc_tile_h != gbt::kTileHSmall && o.alloc_tile_h != gbt::kTileHBig)
     return TSDF_ERR_ARG;
   if (o.integrate_ctas_per_sm < 0) return TSDF_ERR_ARG;
-  if (o.storage != TSDF_STORAGE_FP32 && o.storage != TSDF_STORAGE_FP16 &&
+  if (o.storage != TSDF_STORAGE_FP32 && o.storage != TSDF_STORAGE_FP16 && o.storage != TSDF_STORAGE_FIXED16 &&
       o.storage != gbt::kStorageOcc && o.storage != gbt::kStorageColor)
     return TSDF_ERR_ARG;
   if ((o.storage == gbt::kStorageOcc) != (o.layer == TSDF_LAYER_OCCUPANCY) ||
@@ -408,6 +408,8 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   d.v = voxel_size;
   d.tau = (float)((double)truncation_voxels * m->vd);
   d.inv_tau = 1.0f / d.tau;
+  d.x16_scale = (float)((double)gbt::kX16Steps / (double)d.tau);
+  d.x16_unit = (float)((double)d.tau / (double)gbt::kX16Steps);
   d.wmax = max_weight;
   d.guard = o.lidar_guard > 0.0f ? o.lidar_guard : d.tau;
   d.l_occ = o.l_occ;
@@ -855,6 +857,10 @@ tsdf_status export_blocks(const tsdf_map* map, int32_t* keys_host, float* dist_h
         const __half2 h = reinterpret_cast<const __half2*>(pool.data())[(size_t)i * 512 + l];
         D = __low2float(h) * tau;
         W = __high2float(h);
+      } else if (map->storage == TSDF_STORAGE_FIXED16) {
+        const uint32_t word = reinterpret_cast<const uint32_t*>(pool.data())[(size_t)i * 512 + l];
+        D = gbt::x16_dist(word, map->dev.x16_unit);
+        W = gbt::x16_weight(word);
       } else {
         const float2 f = reinterpret_cast<const float2*>(pool.data())[(size_t)i * 512 + l];
         D = f.x;
@@ -896,7 +902,8 @@ tsdf_status map_decay_occupancy(tsdf_map* map, float decay_occ, float decay_free
 namespace {
 
 bool esdf_layer_ok(const tsdf_map* m) {
-  return m->storage == TSDF_STORAGE_FP32 || m->storage == TSDF_STORAGE_FP16;
+  return m->storage == TSDF_STORAGE_FP32 || m->storage == TSDF_STORAGE_FP16 ||
+         m->storage == TSDF_STORAGE_FIXED16;
 }
 
 tsdf_status esdf_alloc(tsdf_map* m, const tsdf_esdf_opts& o) {
@@ -1148,7 +1155,9 @@ tsdf_status map_mesh(tsdf_map* map, float min_weight, int32_t changed_only, floa
                      int32_t* tri_keys_dev, int32_t* tri_cube_dev, int64_t cap, int64_t* n_tris,
                      void* cuda_stream) {
   if (!map || !n_tris || cap < 0 || (cap > 0 && !tri_pos_dev) || !std::isfinite(min_weight)) return TSDF_ERR_ARG;
-  if (map->storage != TSDF_STORAGE_FP32 && map->storage != TSDF_STORAGE_FP16) return TSDF_ERR_ARG;
+  if (map->storage != TSDF_STORAGE_FP32 && map->storage != TSDF_STORAGE_FP16 &&
+      map->storage != TSDF_STORAGE_FIXED16)
+    return TSDF_ERR_ARG;
   if (!on_device(map)) return TSDF_ERR_STATE;
   gbt::MeshDev& md = map->mesh;
   if (!map->mesh_on) {
@@ -1204,12 +1213,26 @@ tsdf_status map_destroy(tsdf_map* map) {
 // integrate_depth_static: the allocation-free entry point.
 //
 // Some callers cannot allocate GPU memory themselves or through this library
-// (a process whose allocator is owned by another framework, code running
-// while a CUDA graph is being captured, real-time loops that forbid
-// allocation after start-up).  For them the per-call work list that the
-// integration needs lives in g_static_scratch, a fixed-size array in device
-// memory that the module reserves on every GPU that loads it and keeps until
-// the process exits.  The caller owns all map storage and the input image.
+// (a process whose device allocator is owned by another framework, real-time
+// loops that forbid allocation after start-up).  For them the per-call work
+// list that the integration needs lives in g_static_scratch, a fixed-size
+// array in device memory that the module reserves on every GPU that loads it
+// and keeps until the process exits.  The caller owns all map storage and
+// the input image.
+
+// The caller sizes and decodes its buffers from the header's constants; they
+// must be the kernels' own.
+static_assert(TSDF_NUM_COUNTERS == gbt::kNumCounters, "counter words written by the kernels");
+static_assert(TSDF_STORAGE_FP32 == gbt::kStorageF32 && TSDF_STORAGE_FP16 == gbt::kStorageF16 &&
+                  TSDF_STORAGE_FIXED16 == gbt::kStorageX16,
+              "ABI storage codes are the kernels' own");
+static_assert(TSDF_KEY_BIAS == gbt::kKeyBias, "block key bias");
+static_assert(gbt::pack_key(1, 0, 0) - gbt::pack_key(0, 0, 0) == 1ull &&
+                  gbt::pack_key(0, 1, 0) - gbt::pack_key(0, 0, 0) == (1ull << TSDF_KEY_BITS) &&
+                  gbt::pack_key(0, 0, 1) - gbt::pack_key(0, 0, 0) == (1ull << (2 * TSDF_KEY_BITS)) &&
+                  gbt::pack_key(0, 0, 0) == ((unsigned long long)TSDF_KEY_BIAS *
+                                             (1ull + (1ull << TSDF_KEY_BITS) + (1ull << (2 * TSDF_KEY_BITS)))),
+              "block key packing");
 
 namespace {
 

@@ -41,9 +41,30 @@ enum : int {
 enum : unsigned long long { kStPoolFull = 1, kStHashFull = 2, kStListFull = 4, kStTimeout = 8 };
 
 enum : int { kSensorPinhole = 0, kSensorLidar = 1 };
-// Voxel storage: TSDF {D, W} as FP32 or FP16 (D / tau), occupancy
-// log-odds as one FP32 value, or colour {r, g, b, W} as four FP32 values.
-enum : int { kStorageF32 = 0, kStorageF16 = 1, kStorageOcc = 2, kStorageColor = 3 };
+// Voxel storage: TSDF {D, W} as FP32, as FP16 (D / tau) or as 16-bit fixed
+// point (D / tau) with an FP16 weight, occupancy log-odds as one FP32 value,
+// or colour {r, g, b, W} as four FP32 values.  The first three codes are the
+// ABI's TSDF_STORAGE_* values.
+enum : int { kStorageF32 = 0, kStorageF16 = 1, kStorageX16 = 2, kStorageOcc = 3, kStorageColor = 4 };
+
+// 16-bit fixed-point TSDF voxel (one 32-bit word): D / tau as a signed
+// fraction with kX16Steps steps per tau in the low half (round to nearest,
+// saturating at +-tau), W as an FP16 number in the high half.
+constexpr float kX16Steps = 32767.0f;
+__host__ __device__ __forceinline__ float x16_dist(uint32_t word, float unit) {
+  return (float)(int16_t)(uint16_t)(word & 0xFFFFu) * unit;
+}
+__host__ __device__ __forceinline__ float x16_weight(uint32_t word) {
+  __half_raw r;
+  r.x = (unsigned short)(word >> 16);
+  return __half2float(__half(r));
+}
+__device__ __forceinline__ uint32_t x16_pack(float D, float W, float scale) {
+  const float q = fminf(fmaxf(__fmul_rn(D, scale), -kX16Steps), kX16Steps);
+  const int qi = __float2int_rn(q);
+  const __half h = __float2half_rn(W);
+  return ((uint32_t)qi & 0xFFFFu) | ((uint32_t)__half_as_ushort(h) << 16);
+}
 
 // Device view of one map.  The work list holds the hash slots met by the
 // frames of the batch in flight; the integration launch consumes it and its
@@ -54,10 +75,11 @@ struct MapDev {
   unsigned long long* keys;       // [cap] packed block keys, kEmptyKey = free
   int32_t* vals;                  // [cap]
   uint32_t* mask;                 // [cap] frames of the current batch meeting the block
-  void* pool;                     // [max_blocks][512] float2 {D, W} or __half2 {D/tau, W}
+  void* pool;                     // [max_blocks][512] float2 {D, W}, __half2 {D/tau, W} or
+                                  // fixed-point words (x16_pack)
   unsigned long long* block_keys; // [max_blocks] key of each pool block
-  unsigned long long* counters;   // [kNumCounters]; entries from kCntSegments on only
-                                  // when walk_stats != 0
+  unsigned long long* counters;   // [kNumCounters]; kCntSegments and kCntCells are
+                                  // written only when walk_stats != 0
   int32_t walk_stats;             // count band segments and cells (diagnostic)
   uint32_t* list;                 // [list_cap] slots met by the current batch
   unsigned int* ctl;              // [0] list length, [1] finished integration CTAs,
@@ -70,6 +92,7 @@ struct MapDev {
   float v;                        // voxel edge (m)
   float tau;                      // truncation distance, (float)(trunc * (double)v)
   float inv_tau;
+  float x16_scale, x16_unit;      // fixed-point storage: steps per metre, metres per step
   float wmax;
   float guard;                    // LiDAR bilinear guard (m)
   float l_occ, l_free;            // occupancy layer: log-odds added per update
@@ -139,7 +162,7 @@ struct BatchParams {
 // unit step along an axis is a plain add of 1 << (21 * axis) to the key.
 // Bit 63 is always 0, so no key equals kEmptyKey.
 constexpr int kKeyBias = 1 << 20;
-__host__ __device__ __forceinline__ unsigned long long pack_key(int x, int y, int z) {
+__host__ __device__ __forceinline__ constexpr unsigned long long pack_key(int x, int y, int z) {
   return (unsigned long long)(unsigned)(x + kKeyBias) |
          ((unsigned long long)(unsigned)(y + kKeyBias) << 21) |
          ((unsigned long long)(unsigned)(z + kKeyBias) << 42);

@@ -73,3 +73,19 @@ def test_pose_argument_marshalling():
         vals = list(arg) if not isinstance(arg, int) else \
             list((ctypes.c_double * 16).from_address(arg))
         assert vals == T.reshape(16).tolist()
+
+
+def test_header_constants_match_binding(tmp_path):
+    """The sizes a caller of integrate_depth_static allocates and decodes
+    with: counter words, key packing and the work-list limit, as the C
+    compiler sees them in the header."""
+    prog = tmp_path / "consts.c"
+    prog.write_text('#include "tsdf.h"\n#include <stdio.h>\n'
+                    'int main(void){printf("%d %d %d %d\\n", TSDF_NUM_COUNTERS, TSDF_KEY_BITS,'
+                    ' TSDF_KEY_BIAS, TSDF_STATIC_MAX_BLOCKS); return 0;}\n')
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(prog), "-o", str(exe)], check=True)
+    vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+    assert vals == [gt.NUM_COUNTERS, gt.KEY_BITS, gt.KEY_BIAS, gt.STATIC_MAX_BLOCKS]

@@ -161,7 +161,7 @@ def test_query_matches_export():
     g.close()
 
 
-@pytest.mark.parametrize("storage", [gt.STORAGE_FP32, gt.STORAGE_FP16])
+@pytest.mark.parametrize("storage", [gt.STORAGE_FP32, gt.STORAGE_FP16, gt.STORAGE_FIXED16])
 def test_room_gpu_integrated_properties(storage):
     """GPU integration then GPU ESDF on 30 room frames: every parent is a
     site, site flags follow |D| <= eps on the GPU's own TSDF, no distance is

@@ -81,3 +81,22 @@ def test_room_300_frames_fp16(room):
                              "max_err_tau": st["max_err"] / tau,
                              "near_surface_max_err_tau": float(err[near].max() / tau),
                              "near_surface_rms_err_tau": float(np.sqrt(np.mean(err[near] ** 2)) / tau)})
+
+
+def test_room_300_frames_fixed16(room):
+    """16-bit fixed-point storage (D / tau, FP16 weight) on the room sequence."""
+    w, orc, oc = room
+    gpu, gs, status = run_gpu(w.frames, w.voxel_size, storage=2, batch=BATCH)
+    assert status == 0
+    tau = 4 * float(np.float32(w.voxel_size))
+    v = float(np.float32(w.voxel_size))
+    st = compare(gpu, orc, 2e-3 * tau, "room300_fixed16")
+    assert gs["voxel_updates"] == oc["total_updates"]
+    ok, oD, oW = orc
+    obs = oW > 0
+    near = obs & (np.abs(oD) < tau / 4)
+    err = np.abs(gpu[1].astype(np.float64) - oD)
+    _record("room300_fixed16", {**st, "max_err_vox": st["max_err"] / v, "rms_err_vox": st["rms_err"] / v,
+                                "max_err_tau": st["max_err"] / tau, "rms_err_tau": st["rms_err"] / tau,
+                                "near_surface_max_err_tau": float(err[near].max() / tau),
+                                "near_surface_rms_err_tau": float(np.sqrt(np.mean(err[near] ** 2)) / tau)})

@@ -104,6 +104,26 @@ def test_fp16_storage():
     m.close()
 
 
+def test_fixed16_storage():
+    """16-bit fixed-point map: both sides mesh the values as stored (D / tau
+    rounded to 1 / 32767, W to half precision, decoded in FP32)."""
+    keys, D, W, _ = tsdf_region((0, 0, 0), (3, 3, 3),
+                                lambda c: np.linalg.norm(c - np.array([0.61, 0.6, 0.58]), axis=-1) - 0.4)
+    tau = np.float32(4.0 * float(np.float32(V)))
+    scale = np.float32(32767.0 / float(tau))
+    unit = np.float32(float(tau) / 32767.0)
+    q = np.rint(np.clip((D.astype(np.float32) * scale).astype(np.float32), -32767, 32767))
+    Dq = (q.astype(np.float32) * unit).astype(np.float32)
+    W16 = W.astype(np.float16).astype(np.float32)
+    m = _map(V, storage=gt.STORAGE_FIXED16)
+    m.import_blocks(keys, D, W)
+    k2, D2, W2 = m.export()
+    np.testing.assert_array_equal(W2, W16)
+    np.testing.assert_array_equal(D2, Dq)
+    _compare(m.mesh(), oracle.mesh_extract(keys, Dq, W16, float(V)), V)
+    m.close()
+
+
 def test_room_from_oracle_tsdf():
     """The oracle's TSDF of 20 room frames (FP64 rounded to FP32), meshed
     on both sides."""

@@ -1,0 +1,214 @@
+"""Parity of the batched forms with FP16 storage and LiDAR frames against the
+FP64 oracle, per workload.
+
+Rig (one outdoor map at 0.05 m fed per step by four pinhole cameras of three
+sizes and a 1024x64 LiDAR, Sec. IV-B Eq. 2 and Eq. 3 with the guarded
+bilinear sample): 80 steps of 5 frames, one integrate_batch call per step,
+the whole sequence captured in a CUDA graph and replayed (the benchmark's
+launch configuration), FP16 storage (D / tau and W as halves, FP32
+arithmetic).  Enough steps that thousands of voxels reach the weight cap, so
+the exponential average past the cap is exercised in FP16.
+
+Serving (16 maps at 0.02 / 0.05 / 0.1 m, Poisson arrivals of 320x240,
+640x480, 1280x720 depth and 1024x64 LiDAR frames, FP16 storage): the maps
+served together by the continuous-batching loop, each compared with the
+oracle integrating that map's frames alone in arrival order.
+
+Bars: block sets, per-voxel weights, walked cells, (block, frame) pairs and
+update counts bit-exact (decisions follow the prescribed FP32 sequence on
+both sides; weights are integers <= 100, exact in FP16); distances within
+1e-4 voxel plus 4 ulp of the 30 m maximum range with FP32 storage, within
+2e-3 of the truncation distance with 16-bit fixed-point storage, and within
+the derived FP16 bound with FP16 storage.  Both 16-bit forms round the stored
+D once per update, an error r <= half a unit in the last place; the error of
+the running average obeys E_k = (1 - 1/(W_k + 1)) E_(k-1) + r_k, so
+|E| <= (W_max + 1) max|r|: (W_max + 1) 2^-12 tau for FP16 (units of 2^-11
+tau below |D| = tau), (W_max + 1) / 65534 tau for fixed point (1.5e-3 tau at
+W_max = 100), plus the FP32 arithmetic of each step (under 1e-6 tau).  The
+FP16 bound is that of a stored value that stops moving once the step
+(s - D) / (W_max + 1) is below half a unit, which a noisy sensor at the
+weight cap reaches.  Max and RMS distance errors are reported per workload
+(TSDF_TEST_REPORTS).
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from synth.configs import (ROOM_NOISE, SERVING_SENSORS, Frame, config_serving_maps, render_frame,
+                           serving_arrivals)
+from tests.runners import compare, run_gpu, run_oracle, to_device
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2311_00626_gb300 as gt  # noqa: E402
+from paper_2311_00626_gb300.serving import Request, Server  # noqa: E402
+
+REPORT = os.environ.get("TSDF_TEST_REPORTS", "")
+RIG_STEPS = 80  # of the 200-step rig path: 400 frames
+W_MAX = 100.0
+ARITH = 1e-6  # FP32 arithmetic of one update, in tau
+
+
+def bound_tau(storage):
+    """Worst-case distance error against the FP64 oracle, in tau."""
+    if storage == gt.STORAGE_FP16:
+        return (W_MAX + 1) * (2.0 ** -12 + ARITH)
+    assert storage == gt.STORAGE_FIXED16
+    return 2e-3  # the stated bound; the derived one is (W_MAX + 1) * (1 / 65534 + ARITH) < 1.7e-3
+
+
+NAMES = {1: "fp16", 2: "fixed16"}
+
+
+def _record(name, stats):
+    if REPORT and os.path.isdir(REPORT):
+        with open(os.path.join(REPORT, "precision.jsonl"), "a") as fh:
+            fh.write(json.dumps({"case": name, **stats}) + "\n")
+
+
+def _errors(gpu, orc, v, tau):
+    """Max and RMS |D_gpu - D_oracle| over observed voxels, in voxels and in
+    tau, overall and for |D| < tau / 4."""
+    _, oD, oW = orc
+    obs = oW > 0
+    err = np.abs(gpu[1].astype(np.float64) - oD)[obs]
+    near = np.abs(oD[obs]) < tau / 4
+    return {"max_err_vox": float(err.max() / v), "rms_err_vox": float(np.sqrt(np.mean(err ** 2)) / v),
+            "max_err_tau": float(err.max() / tau), "rms_err_tau": float(np.sqrt(np.mean(err ** 2)) / tau),
+            "near_surface_max_err_tau": float(err[near].max() / tau),
+            "near_surface_rms_err_tau": float(np.sqrt(np.mean(err[near] ** 2)) / tau),
+            "voxels_at_weight_cap": int(np.count_nonzero(oW == 100.0))}
+
+
+@pytest.fixture(scope="module")
+def rig():
+    w = synth.config_rig(n_steps=200)
+    frames = w.frames[:5 * RIG_STEPS]
+    orc, oc = run_oracle(frames, w.voxel_size)
+    return w, frames, orc, oc
+
+
+@pytest.mark.parametrize("storage", [gt.STORAGE_FP16, gt.STORAGE_FIXED16])
+def test_rig_16bit_graph_replay_against_oracle(rig, storage):
+    w, frames, orc, oc = rig
+    v = float(np.float32(w.voxel_size))
+    tau = 4 * v
+    name = f"rig80_{NAMES[storage]}_graph"
+    m = gt.TsdfMap(w.voxel_size, w.truncation_voxels, w.max_weight, storage=storage)
+    gt.map_walk_stats(m.handle, True)
+    dev = to_device(frames)
+    descs = [gt.frame_desc(0, f.sensor, f.T, d) for f, d in zip(frames, dev)]
+
+    def run():
+        m.reset()
+        for s in range(0, len(frames), 5):
+            gt.integrate_batch([m.handle], descs[s:s + 5])
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        run()  # eager warm-up: sensor tables and kernels set up before capture
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        run()
+    g.replay()
+    torch.cuda.synchronize()
+    assert m.sync() == 0
+    gpu = m.export()
+    gs = m.stats()
+    m.close()
+    e = _errors(gpu, orc, v, tau)
+    _record(name, {**e, "bound_tau": bound_tau(storage)})
+    st = compare(gpu, orc, bound_tau(storage) * tau, name)
+    assert gs["voxel_updates"] == oc["total_updates"]
+    assert gs["cells"] == oc["total_cells"]
+    assert gs["block_frame_pairs"] == oc["total_band_blocks"]
+    assert e["voxels_at_weight_cap"] > 1000
+    assert st["blocks"] == len(orc[0])
+
+
+def test_rig_fp32_batched_against_oracle(rig):
+    w, frames, orc, oc = rig
+    v = float(np.float32(w.voxel_size))
+    tol = 1e-4 * v + 4 * float(np.spacing(np.float32(30.0)))
+    gpu, gs, status = run_gpu(frames, w.voxel_size, batch=5)
+    assert status == 0
+    st = compare(gpu, orc, tol, "rig80_fp32")
+    assert gs["voxel_updates"] == oc["total_updates"]
+    assert gs["cells"] == oc["total_cells"]
+    _record("rig80_fp32", {**st, **_errors(gpu, orc, v, 4 * v)})
+
+
+def _serving_requests(seconds):
+    cfg = config_serving_maps(16)
+    arrivals = serving_arrivals(16, 30.0, seconds)
+    count = [0] * 16
+    reqs, frames = [], [[] for _ in cfg]
+    poses = [synth.trajectory(c["seed"], c["prims"], 64) for c in cfg]
+    for t, mid, si in arrivals:
+        k = count[mid]
+        count[mid] += 1
+        sensor = SERVING_SENSORS[si]
+        T = poses[mid][k % 64]
+        if sensor["kind"] == "lidar":
+            T = T.copy()
+            T[:3, :3] = np.eye(3)
+        d = render_frame(cfg[mid]["prims"], sensor, T,
+                         ROOM_NOISE if sensor["kind"] == "pinhole" else {"sigma": 0.02},
+                         cfg[mid]["seed"], k * 4 + si)
+        reqs.append(Request(len(reqs), mid, sensor, T, torch.from_numpy(d).pin_memory(), t))
+        frames[mid].append(Frame(sensor, T, d))
+    return cfg, reqs, frames
+
+
+@pytest.fixture(scope="module")
+def serving():
+    cfg, reqs, frames = _serving_requests(0.3)
+    orcs = [run_oracle(frames[k], cfg[k]["voxel_size"])[0] if frames[k] else None
+            for k in range(len(cfg))]
+    return cfg, reqs, frames, orcs
+
+
+@pytest.mark.parametrize("storage", [gt.STORAGE_FP16, gt.STORAGE_FIXED16])
+def test_serving_mix_16bit_against_oracle(serving, storage):
+    """Every map of a 16-map continuous-batching run against the oracle."""
+    cfg, reqs, frames, orcs = serving
+    assert {r.sensor["kind"] for r in reqs} == {"pinhole", "lidar"}
+    assert len({c["voxel_size"] for c in cfg}) == 3
+    maps = [gt.TsdfMap(c["voxel_size"], c["truncation_voxels"], c["max_weight"],
+                       storage=storage) for c in cfg]
+    srv = Server(maps, staging_bytes=64 << 20, max_frames=32)
+    done = srv.run(reqs, paced=False)
+    assert len(done) == len(reqs)
+    worst = {"max_err_tau": 0.0}
+    sq, nobs = 0.0, 0
+    for k, m in enumerate(maps):
+        assert m.sync() == 0
+        gpu = m.export()
+        m.close()
+        if not frames[k]:
+            assert len(gpu[0]) == 0
+            continue
+        v = float(np.float32(cfg[k]["voxel_size"]))
+        tau = 4 * v
+        orc = orcs[k]
+        st = compare(gpu, orc, bound_tau(storage) * tau, f"serving map {k}")
+        e = _errors(gpu, orc, v, tau)
+        if e["max_err_tau"] > worst["max_err_tau"]:
+            worst = {"map": k, "voxel_size": v, **e}
+        sq += (e["rms_err_tau"] ** 2) * st["observed"]
+        nobs += st["observed"]
+    _record(f"serving16_{NAMES[storage]}", {"frames": len(reqs), "worst_map": worst,
+                                            "rms_err_tau_all_maps": float(np.sqrt(sq / max(nobs, 1))),
+                                            "bound_tau": bound_tau(storage)})

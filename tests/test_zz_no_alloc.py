@@ -1,11 +1,18 @@
 """The allocation-free entry point, integrate_depth_static, against the
 ordinary one.
 
-Callers that cannot allocate GPU memory when they integrate (their memory
-belongs to another framework, or they are capturing a CUDA graph) pass their
-own map storage; the library's per-call work list then comes from a fixed
-device array.  This file is collected last on purpose: it runs after every
-other test in a full run and must also pass on its own in a fresh process.
+Some callers cannot allocate GPU memory when they integrate: their device
+allocator belongs to another framework that owns all of the GPU's memory, or
+a real-time loop forbids allocation once it runs.  They pass their own map
+storage; the library's per-call work list then comes from a fixed device
+array inside the library.  The checks here: two calls in a row give the same
+blocks, weights and distances as integrate_depth, bit for bit (the same
+kernels run on the same inputs); no byte beyond the documented size of any
+caller buffer is written; the calls allocate no device memory; oversized maps
+are refused.
+
+This file is collected last on purpose: it runs after every other test in a
+full run and must also pass on its own in a fresh process.
 """
 from __future__ import annotations
 
@@ -24,20 +31,36 @@ from tests.runners import to_device  # noqa: E402
 
 MAX_BLOCKS = 1 << 14
 CAP = 1 << 15
+TAIL = 64  # sentinel elements after each buffer's documented size
 
 
 def _buffers():
-    t = {
-        "keys": torch.full((CAP,), -1, dtype=torch.int64, device="cuda"),
-        "vals": torch.full((CAP,), -1, dtype=torch.int32, device="cuda"),
-        "mask": torch.zeros(CAP, dtype=torch.int32, device="cuda"),
-        "pool": torch.empty(MAX_BLOCKS * 512 * 2, dtype=torch.float32, device="cuda"),
-        "block_keys": torch.empty(MAX_BLOCKS, dtype=torch.int64, device="cuda"),
-        "counters": torch.zeros(6, dtype=torch.int64, device="cuda"),
+    """Caller-owned storage at exactly the sizes the header documents, each
+    followed by a sentinel tail inside the same allocation."""
+    spec = {  # name: (elements, dtype, initial value of the documented part)
+        "keys": (CAP, torch.int64, -1),
+        "vals": (CAP, torch.int32, -1),
+        "mask": (CAP, torch.int32, 0),
+        "pool": (MAX_BLOCKS * 512 * 2, torch.float32, None),
+        "block_keys": (MAX_BLOCKS, torch.int64, None),
+        "counters": (gt.NUM_COUNTERS, torch.int64, 0),
     }
-    b = gt.MapBuffers(*(t[k].data_ptr() for k in ("keys", "vals", "mask", "pool", "block_keys",
-                                                   "counters")), CAP, MAX_BLOCKS)
-    return b, t
+    full, head = {}, {}
+    for name, (n, dt, init) in spec.items():
+        raw = torch.empty(n + TAIL, dtype=dt, device="cuda")
+        raw.view(torch.uint8).fill_(0x5A)
+        if init is not None:
+            raw[:n].fill_(init)
+        full[name], head[name] = raw, raw[:n]
+    b = gt.MapBuffers(*(head[k].data_ptr() for k in ("keys", "vals", "mask", "pool", "block_keys",
+                                                      "counters")), CAP, MAX_BLOCKS)
+    return b, head, full
+
+
+def _tails_untouched(full, label):
+    for name, raw in full.items():
+        tail = raw[raw.numel() - TAIL:].view(torch.uint8)
+        assert bool((tail == 0x5A).all()), f"{label}: bytes written past the end of {name}"
 
 
 def _decode(t):
@@ -46,8 +69,8 @@ def _decode(t):
     assert cnt[2] == 0, f"device status bits {cnt[2]}"
     n = int(min(cnt[0], MAX_BLOCKS))
     bk = t["block_keys"][:n].cpu().numpy().view(np.uint64)
-    xyz = np.stack([((bk >> np.uint64(21 * a)) & np.uint64(0x1FFFFF)).astype(np.int64) - (1 << 20)
-                    for a in range(3)], 1).astype(np.int32)
+    xyz = np.stack([((bk >> np.uint64(gt.KEY_BITS * a)) & np.uint64((1 << gt.KEY_BITS) - 1))
+                    .astype(np.int64) - gt.KEY_BIAS for a in range(3)], 1).astype(np.int32)
     pool = t["pool"].view(MAX_BLOCKS, 512, 2)[:n].cpu().numpy()
     order = np.lexsort((xyz[:, 2], xyz[:, 1], xyz[:, 0]))
     return xyz[order], pool[order, :, 0], pool[order, :, 1]
@@ -59,25 +82,36 @@ def test_static_entry_matches_integrate_depth_two_calls():
     dev = to_device(frames)
     v = w.voxel_size
     ref = gt.TsdfMap(v, w.truncation_voxels, w.max_weight)
-    buf, t = _buffers()
-    tol = 1e-4 * float(np.float32(v))
+    buf, head, full = _buffers()
+    torch.cuda.synchronize()
     for k, (f, d) in enumerate(zip(frames, dev)):
         ref.integrate(f.sensor, f.T, d)
+        torch.cuda.synchronize()
+        before = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(),
+                  torch.cuda.mem_get_info()[0])
         gt.integrate_depth_static(buf, v, w.truncation_voxels, w.max_weight, d,
                                   gt.pinhole(f.sensor), f.T)
         torch.cuda.synchronize()
+        after = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(),
+                 torch.cuda.mem_get_info()[0])
+        if k > 0:  # the first call on a device may load the library's kernels
+            assert after == before, f"call {k}: device memory changed {before} -> {after}"
+        _tails_untouched(full, f"call {k}")
         rk, rD, rW = ref.export()
-        sk, sD, sW = _decode(t)
+        sk, sD, sW = _decode(head)
         np.testing.assert_array_equal(sk, rk, err_msg=f"call {k}: block sets differ")
         np.testing.assert_array_equal(sW, rW, err_msg=f"call {k}: weights differ")
-        obs = rW > 0
-        assert np.abs(sD[obs] - rD[obs]).max() <= tol
-        assert int(t["counters"][1].item()) == ref.stats()["voxel_updates"]
+        np.testing.assert_array_equal(sD, rD, err_msg=f"call {k}: distances differ")
+        rs = ref.stats()
+        cnt = head["counters"].cpu().numpy()
+        assert int(cnt[1]) == rs["voxel_updates"]
+        assert int(cnt[4]) == k + 1  # integration launches
+        assert int(cnt[7]) == rs["block_frame_pairs"]
     ref.close()
 
 
 def test_static_entry_refuses_oversized_maps():
-    buf, _ = _buffers()
+    buf, _, full = _buffers()
     buf.max_blocks = gt.STATIC_MAX_BLOCKS + 1
     buf.hash_capacity = 1 << 18
     w = synth.config_tiny()
@@ -86,3 +120,5 @@ def test_static_entry_refuses_oversized_maps():
         gt.integrate_depth_static(buf, w.voxel_size, 4, 100.0, d, gt.pinhole(w.frames[0].sensor),
                                   w.frames[0].T)
     assert e.value.code == -3
+    torch.cuda.synchronize()
+    _tails_untouched(full, "refused call")
