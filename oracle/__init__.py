@@ -77,6 +77,7 @@ def _load():
             lib.esdf_orc_create.argtypes = [F, F, F, I]
             lib.esdf_orc_create.restype = P
             lib.esdf_orc_destroy.argtypes = [P]
+            lib.esdf_orc_set_occupancy.argtypes = [P]
             lib.esdf_orc_update.argtypes = [P, P, P, P, L, P]
             lib.esdf_orc_update.restype = L
             lib.esdf_orc_num_blocks.argtypes = [P]
@@ -230,11 +231,16 @@ def esdf_offsets(states: np.ndarray) -> np.ndarray:
 class EsdfOracle:
     """Incremental ESDF over TSDF blocks (Sec. IV-C), integer parent offsets."""
 
-    def __init__(self, voxel_size: float, site_eps: float, min_weight: float, max_dist_vox: int):
+    def __init__(self, voxel_size: float, site_eps: float, min_weight: float, max_dist_vox: int,
+                 occupancy: bool = False):
+        """occupancy: D holds log-odds and sites follow the occupancy rule
+        (occupied voxels next to free ones)."""
         self._lib = _load()
         self._h = self._lib.esdf_orc_create(voxel_size, site_eps, min_weight, max_dist_vox)
         if not self._h:
             raise ValueError("bad ESDF parameters")
+        if occupancy:
+            self._lib.esdf_orc_set_occupancy(self._h)
 
     def close(self):
         if self._h:

@@ -32,6 +32,15 @@
  *      +y, -z, +z order), reading the neighbours as they were before this
  *      step; the blocks that changed form the next update set.
  *
+ * Occupancy layers (Sec. IV-C: an occupancy voxel is a site if it is
+ * adjacent to free voxels).  With set_occupancy the D input holds log-odds
+ * l (W is ignored): a voxel is occupied if l > 0, free if l < 0 and unknown
+ * if l == 0 (probability 1/2, never observed or decayed back); observed =
+ * occupied or free; inside = occupied; site = occupied with a free voxel
+ * among its six face neighbours (a neighbour in a block absent from the
+ * input is unknown).  A voxel's site status then depends on the next block,
+ * so stage 2 marks the changed blocks and their face neighbours.
+ *
  * A voxel p "tries" the parent of a neighbour q when p is observed and not a
  * site and q has a parent: the candidate offset is (q + parent_q) - p; it is
  * taken if its squared length is at most max_dist^2 and strictly smaller
@@ -78,6 +87,7 @@ struct Block {
 struct Esdf {
   float v = 0.0f, site_eps = 0.0f, min_weight = 0.0f;
   int32_t max_dist = 0;
+  bool occupancy = false;  // sites by the occupancy rule instead of |D| <= site_eps
   std::unordered_map<Key, std::unique_ptr<Block>, KeyHash> blocks;
   int64_t iterations = 0, swept = 0, pulled = 0, cleared = 0;
 };
@@ -162,11 +172,15 @@ void* esdf_orc_create(float voxel_size, float site_eps, float min_weight, int32_
 
 void esdf_orc_destroy(void* h) { delete static_cast<Esdf*>(h); }
 
+/* Switch to the occupancy site rule (before the first update). */
+void esdf_orc_set_occupancy(void* h) { static_cast<Esdf*>(h)->occupancy = true; }
+
 /*
  * One update.  keys int32 [n][3], D and W float32 [n][512] (voxel x + 8 y +
- * 64 z): the TSDF blocks; changed uint8 [n]: blocks changed since the last
- * update (only their D and W are read).  Returns the number of lowering
- * iterations.
+ * 64 z): the TSDF blocks (or occupancy log-odds in D); changed uint8 [n]:
+ * blocks changed since the last update (only their values, and for an
+ * occupancy layer their face neighbours' values, are read).  Returns the
+ * number of lowering iterations.
  */
 int64_t esdf_orc_update(void* h, const int32_t* keys, const float* D, const float* W, int64_t n,
                         const uint8_t* changed) {
@@ -174,9 +188,32 @@ int64_t esdf_orc_update(void* h, const int32_t* keys, const float* D, const floa
   const int64_t max2 = (int64_t)e.max_dist * e.max_dist;
   std::vector<Key> upd_list, clr_list;
   std::unordered_set<Key, KeyHash> upd, clr;
+  static const int kFace[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+  // blocks to mark: the changed ones, and for an occupancy layer their face
+  // neighbours too (a site test reads across the faces)
+  std::vector<uint8_t> mark(changed, changed + n);
+  std::unordered_map<Key, int64_t, KeyHash> index;
+  if (e.occupancy) {
+    for (int64_t i = 0; i < n; ++i) index[Key{keys[3 * i], keys[3 * i + 1], keys[3 * i + 2]}] = i;
+    for (int64_t i = 0; i < n; ++i) {
+      if (!changed[i]) continue;
+      for (const auto& f : kFace) {
+        auto it = index.find(Key{keys[3 * i] + f[0], keys[3 * i + 1] + f[1], keys[3 * i + 2] + f[2]});
+        if (it != index.end()) mark[it->second] = 1;
+      }
+    }
+  }
+  // log-odds of the voxel at global index g (0 = unknown when its block is absent)
+  auto occ_at = [&](int64_t gx, int64_t gy, int64_t gz) -> float {
+    auto fl = [](int64_t a) { return a >= 0 ? a / 8 : -((-a + 7) / 8); };
+    const Key k{fl(gx), fl(gy), fl(gz)};
+    auto it = index.find(k);
+    if (it == index.end()) return 0.0f;
+    return D[512 * it->second + lin((int)(gx - 8 * k.x), (int)(gy - 8 * k.y), (int)(gz - 8 * k.z))];
+  };
   // 1-2. allocate and mark sites in the changed blocks
   for (int64_t i = 0; i < n; ++i) {
-    if (!changed[i]) continue;
+    if (!mark[i]) continue;
     const Key k{keys[3 * i], keys[3 * i + 1], keys[3 * i + 2]};
     auto& slot = e.blocks[k];
     if (!slot) {
@@ -186,10 +223,21 @@ int64_t esdf_orc_update(void* h, const int32_t* keys, const float* D, const floa
     Block& b = *slot;
     bool any = false, lost_site = false;
     for (int l = 0; l < 512; ++l) {
-      const float d = D[512 * i + l], w = W[512 * i + l];
-      const bool obs = w >= e.min_weight;
-      const bool site = obs && std::fabs(d) <= e.site_eps;
-      const bool inside = obs && d < 0.0f;
+      const float d = D[512 * i + l];
+      bool obs, site, inside;
+      if (e.occupancy) {
+        obs = d != 0.0f;
+        inside = d > 0.0f;
+        bool free_nbr = false;
+        const int64_t gx = 8 * k.x + (l & 7), gy = 8 * k.y + ((l >> 3) & 7), gz = 8 * k.z + (l >> 6);
+        for (const auto& f : kFace) free_nbr = free_nbr || occ_at(gx + f[0], gy + f[1], gz + f[2]) < 0.0f;
+        site = inside && free_nbr;
+      } else {
+        const float w = W[512 * i + l];
+        obs = w >= e.min_weight;
+        site = obs && std::fabs(d) <= e.site_eps;
+        inside = obs && d < 0.0f;
+      }
       const uint32_t old = b.s[l];
       uint32_t s = old;
       if (site) {
@@ -241,7 +289,6 @@ int64_t esdf_orc_update(void* h, const int32_t* keys, const float* D, const floa
   // 4. lower until no block changes
   int64_t iters = 0;
   std::vector<Key> S = upd_list;
-  static const int kFace[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
   while (!S.empty()) {
     ++iters;
     for (const Key& k : S) sweep_block(*find(e, k), max2);
