@@ -367,9 +367,16 @@ typedef struct {
  * from the adjacent voxel across the face, all reading the states before the
  * exchange.  A parent is taken only if strictly shorter and within
  * max_dist.  The first call allocates the layer (8 KiB per pool block) and
- * fixes the parameters; later calls must pass the same ones.  TSDF maps
- * only (FP32 or FP16 storage).  Enqueued on cuda_stream; waits for the
- * stream after every four iterations to test for convergence.
+ * fixes the parameters; later calls must pass the same ones.  TSDF maps (any
+ * storage) and occupancy maps.  On an occupancy map (Sec. IV-C: an occupancy
+ * voxel is a site if it is adjacent to free voxels) a voxel with log-odds
+ * l > 0 is occupied (inside), l < 0 free, l = 0 unknown; a site is an
+ * occupied voxel with a free voxel among its six face neighbours (a voxel of
+ * a missing block is unknown); site_eps and min_weight are not used; the
+ * blocks marked are the changed ones and their face neighbours, and a
+ * map_decay_occupancy call counts as a change of every block it alters.
+ * Enqueued on cuda_stream; waits for the stream after every four iterations
+ * to test for convergence.
  */
 tsdf_status map_esdf_update(tsdf_map* map, const tsdf_esdf_opts* opts, void* cuda_stream);
 

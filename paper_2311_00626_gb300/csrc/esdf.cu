@@ -8,7 +8,10 @@
 //                      update (the dirty flags the integration sets) and
 //                      reset voxels whose site status, observation or side
 //                      changed; collect the update set and the blocks where
-//                      a site disappeared
+//                      a site disappeared (occupancy layers: the face-
+//                      neighbour table first, then esdf_occ_spread_kernel
+//                      and esdf_occ_mark_kernel, whose site test reads
+//                      across block faces)
 //   esdf_clear_kernel  in every block near one of the latter, drop parents
 //                      that are no longer sites
 //   esdf_nbr_kernel    the face-neighbour table of every block
@@ -95,6 +98,36 @@ __device__ __forceinline__ bool bit_set(const uint32_t* bits, uint32_t b) {
 
 // ------------------------------------------------------------- mark sites
 
+// New state of a voxel from its observation, site and side: a new site
+// takes itself as parent; a voxel that stops being a site, becomes
+// observed or changes sides loses its parent (lost: a site disappeared).
+__device__ __forceinline__ uint32_t marked_state(uint32_t old, bool obs, bool site, bool inside, bool& lost) {
+  if (site) return kEsdfObs | kEsdfSite | kEsdfPar | (inside ? kEsdfInside : 0u);
+  if (old & kEsdfSite) {
+    lost = true;
+    return obs ? (kEsdfObs | (inside ? kEsdfInside : 0u)) : 0u;
+  }
+  if (!obs) return 0u;
+  if (!(old & kEsdfObs) || ((old & kEsdfInside) != 0u) != inside) return kEsdfObs | (inside ? kEsdfInside : 0u);
+  return old;
+}
+
+// Update-set and lost-site bookkeeping of a marked block (lane 0).
+__device__ __forceinline__ void mark_done(const MapDev& m, const EsdfDev& e, uint32_t p, uint32_t gen, bool any,
+                                          bool lost) {
+  if (any) add_update(e, e.list[0], e.cnt, p, gen);
+  if (lost) {
+    e.clist[atomicAdd(e.cnt + 2, 1u)] = p;
+    const unsigned long long key = m.block_keys[p];
+    const int G = parent_reach(e) + 1;
+    const int cx = key_coord(key, 0) + kCoordBias, cy = key_coord(key, 1) + kCoordBias,
+              cz = key_coord(key, 2) + kCoordBias;
+    const uint32_t l = near_bit(cx, cy, cz), c = near_bit(cx / G, cy / G, cz / G);
+    atomicOr(e.bits + (l >> 5), 1u << (l & 31));
+    atomicOr(e.bits + kEsdfBitWords + (c >> 5), 1u << (c & 31));
+  }
+}
+
 // One warp per pool block, 16 voxels per lane (voxels 128 j + 4 lane + i),
 // read and written as 16-byte vectors.
 __global__ void __launch_bounds__(kEsdfThreads)
@@ -139,21 +172,8 @@ __global__ void __launch_bounds__(kEsdfThreads)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const bool obs = W[i] >= e.min_weight;
-        const bool site = obs && fabsf(D[i]) <= e.site_eps;
-        const bool inside = obs && D[i] < 0.0f;
-        uint32_t s = old[i];
-        if (site) {
-          s = kEsdfObs | kEsdfSite | kEsdfPar | (inside ? kEsdfInside : 0u);
-        } else if (old[i] & kEsdfSite) {
-          s = obs ? (kEsdfObs | (inside ? kEsdfInside : 0u)) : 0u;
-          lost = true;
-        } else if (!obs) {
-          s = 0u;
-        } else if (!(old[i] & kEsdfObs) || ((old[i] & kEsdfInside) != 0u) != inside) {
-          s = kEsdfObs | (inside ? kEsdfInside : 0u);
-        }
-        nw[i] = s;
-        changed = changed || s != old[i];
+        nw[i] = marked_state(old[i], obs, obs && fabsf(D[i]) <= e.site_eps, obs && D[i] < 0.0f, lost);
+        changed = changed || nw[i] != old[i];
       }
       if (changed) stb[32 * j] = make_uint4(nw[0], nw[1], nw[2], nw[3]);
       any = any || changed;
@@ -162,17 +182,88 @@ __global__ void __launch_bounds__(kEsdfThreads)
     lost = __any_sync(0xffffffffu, lost);
     if (lane == 0) {
       m.dirty[p] &= (uint8_t)~kDirtyEsdf;
-      if (any) add_update(e, e.list[0], e.cnt, p, gen);
-      if (lost) {
-        e.clist[atomicAdd(e.cnt + 2, 1u)] = p;
-        const unsigned long long key = m.block_keys[p];
-        const int G = parent_reach(e) + 1;
-        const int cx = key_coord(key, 0) + kCoordBias, cy = key_coord(key, 1) + kCoordBias,
-                  cz = key_coord(key, 2) + kCoordBias;
-        const uint32_t l = near_bit(cx, cy, cz), c = near_bit(cx / G, cy / G, cz / G);
-        atomicOr(e.bits + (l >> 5), 1u << (l & 31));
-        atomicOr(e.bits + kEsdfBitWords + (c >> 5), 1u << (c & 31));
+      mark_done(m, e, p, gen, any, lost);
+    }
+  }
+}
+
+// Occupancy layers (Sec. IV-C: an occupancy voxel is a site if it is
+// adjacent to free voxels).  Log-odds l > 0 is occupied, l < 0 free, l = 0
+// unknown (never observed, or decayed back to probability 1/2); observed =
+// occupied or free, inside = occupied, site = occupied with a free voxel
+// among its six face neighbours.  Neighbours across a block face are read
+// through the face-neighbour table (a missing block is unknown), so a block
+// is marked when it changed or one of its face neighbours did.
+
+// Flag the face neighbours of every changed block.  Every writer of a byte
+// here sets the same bit, so the unsynchronised read-modify-writes agree.
+__global__ void esdf_occ_spread_kernel(const MapDev m, const EsdfDev e) {
+  const uint32_t nb = n_blocks(m);
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < nb; p += gridDim.x * blockDim.x) {
+    if (!(m.dirty[p] & kDirtyEsdf)) continue;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const int q = e.nbr[6 * p + f];
+      if (q >= 0) m.dirty[q] |= kDirtyNbr;
+    }
+  }
+}
+
+// One warp per flagged block: the block's log-odds staged in shared memory,
+// 16 voxels per lane (voxels 128 j + 4 lane + i) as in esdf_mark_kernel.
+__global__ void __launch_bounds__(kEsdfThreads)
+    esdf_occ_mark_kernel(const MapDev m, const EsdfDev e, uint32_t gen) {
+  constexpr int kWarps = kEsdfThreads / 32;
+  __shared__ __align__(16) float s_l[kWarps][512];
+  const uint32_t nb = n_blocks(m);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float* pool = reinterpret_cast<const float*>(m.pool);
+  float* sl = s_l[warp];
+  for (uint32_t p = blockIdx.x * kWarps + warp; p < nb; p += gridDim.x * kWarps) {
+    if (!(m.dirty[p] & (kDirtyEsdf | kDirtyNbr))) continue;  // same value for every lane
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      reinterpret_cast<float4*>(sl)[32 * j + lane] = reinterpret_cast<const float4*>(pool)[(size_t)p * 128 + 32 * j + lane];
+    const int mine = lane < 6 ? e.nbr[6 * p + lane] : -1;
+    int q[6];  // face neighbours -x, +x, -y, +y, -z, +z
+#pragma unroll
+    for (int f = 0; f < 6; ++f) q[f] = __shfl_sync(0xffffffffu, mine, f);
+    __syncwarp();
+    uint4* stb = reinterpret_cast<uint4*>(e.st + (size_t)p * 512) + lane;
+    bool any = false, lost = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint4 o4 = stb[32 * j];
+      const uint32_t old[4] = {o4.x, o4.y, o4.z, o4.w};
+      uint32_t nw[4];
+      bool changed = false;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int l = 128 * j + 4 * lane + i;
+        const int c[3] = {l & 7, (l >> 3) & 7, l >> 6};
+        const float v = sl[l];
+        bool free_nbr = false;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+          const int axis = f >> 1, d = (f & 1) ? 1 : -1, stride = axis == 0 ? 1 : (axis == 1 ? 8 : 64);
+          const int cn = c[axis] + d;
+          float w;
+          if (cn >= 0 && cn < 8) w = sl[l + d * stride];
+          else w = q[f] >= 0 ? pool[(size_t)q[f] * 512 + l - d * 7 * stride] : 0.0f;
+          free_nbr = free_nbr || w < 0.0f;
+        }
+        const bool obs = v != 0.0f, inside = v > 0.0f;
+        nw[i] = marked_state(old[i], obs, inside && free_nbr, inside, lost);
+        changed = changed || nw[i] != old[i];
       }
+      if (changed) stb[32 * j] = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+      any = any || changed;
+    }
+    any = __any_sync(0xffffffffu, any);  // also: every lane is done with sl and dirty[p]
+    lost = __any_sync(0xffffffffu, lost);
+    if (lane == 0) {
+      m.dirty[p] &= (uint8_t)~(kDirtyEsdf | kDirtyNbr);
+      mark_done(m, e, p, gen, any, lost);
     }
   }
 }
@@ -524,13 +615,20 @@ int grid_for(int per_sm) {
 }  // namespace
 
 cudaError_t launch_esdf_mark(const MapDev& m, const EsdfDev& e, uint32_t gen, cudaStream_t s) {
-  esdf_mark_kernel<<<grid_for(16), kEsdfThreads, 0, s>>>(m, e, gen);
+  if (m.storage == kStorageOcc) {
+    // occupancy sites read across block faces: the neighbour table first
+    esdf_nbr_kernel<<<grid_for(4), 256, 0, s>>>(m, e);
+    esdf_occ_spread_kernel<<<grid_for(4), 256, 0, s>>>(m, e);
+    esdf_occ_mark_kernel<<<grid_for(16), kEsdfThreads, 0, s>>>(m, e, gen);
+  } else {
+    esdf_mark_kernel<<<grid_for(16), kEsdfThreads, 0, s>>>(m, e, gen);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_esdf_clear(const MapDev& m, const EsdfDev& e, uint32_t gen, cudaStream_t s) {
   esdf_clear_kernel<<<grid_for(10), kEsdfThreads, 0, s>>>(m, e, gen);  // 48 registers: 10 CTAs per SM
-  esdf_nbr_kernel<<<grid_for(4), 256, 0, s>>>(m, e);
+  if (m.storage != kStorageOcc) esdf_nbr_kernel<<<grid_for(4), 256, 0, s>>>(m, e);  // built before marking otherwise
   return cudaGetLastError();
 }
 

@@ -923,11 +923,16 @@ __global__ void decay_kernel(const MapDev m, float d_occ, float d_free) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
        i += (size_t)gridDim.x * blockDim.x) {
     float4 l = pool[i];
+    const float4 before = l;
     float* c = &l.x;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       c[k] = c[k] > 0.0f ? fmaxf(c[k] - d_occ, 0.0f) : (c[k] < 0.0f ? fminf(c[k] + d_free, 0.0f) : c[k]);
     pool[i] = l;
+    // a changed block is due for the next ESDF update and mesh extraction
+    // (all writers of a block's flag byte set the same bits)
+    if (m.dirty && (l.x != before.x || l.y != before.y || l.z != before.z || l.w != before.w))
+      m.dirty[i / 128] |= kDirtyEsdf | kDirtyMesh;
   }
 }
 

@@ -903,7 +903,7 @@ namespace {
 
 bool esdf_layer_ok(const tsdf_map* m) {
   return m->storage == TSDF_STORAGE_FP32 || m->storage == TSDF_STORAGE_FP16 ||
-         m->storage == TSDF_STORAGE_FIXED16;
+         m->storage == TSDF_STORAGE_FIXED16 || m->storage == gbt::kStorageOcc;
 }
 
 tsdf_status esdf_alloc(tsdf_map* m, const tsdf_esdf_opts& o) {

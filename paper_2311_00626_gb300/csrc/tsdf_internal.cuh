@@ -101,7 +101,8 @@ struct MapDev {
   uint8_t* dirty;                 // [max_blocks] kDirtyEsdf / kDirtyMesh: changed since the
                                   // last ESDF update / mesh extraction (may be null)
 };
-enum : uint8_t { kDirtyEsdf = 1, kDirtyMesh = 2 };
+// kDirtyNbr: a face neighbour changed (occupancy ESDF sites read across faces)
+enum : uint8_t { kDirtyEsdf = 1, kDirtyMesh = 2, kDirtyNbr = 4 };
 
 // ESDF layer of a map (Sec. IV-C), indexed like the pool.  State word per
 // voxel: parent offset x, y, z as 9-bit two's complement in bits 0-8, 9-17,

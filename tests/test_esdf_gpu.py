@@ -200,10 +200,10 @@ def test_room_gpu_integrated_properties(storage):
 
 
 def test_esdf_argument_errors():
-    occ = gt.TsdfMap(float(V), layer=gt.LAYER_OCCUPANCY)
+    col = gt.TsdfMap(float(V), layer=gt.LAYER_COLOR)  # colour maps have no ESDF
     with pytest.raises(gt.TsdfError):
-        occ.esdf_update()
-    occ.close()
+        col.esdf_update()
+    col.close()
     g = gt.TsdfMap(float(V))
     with pytest.raises(gt.TsdfError):  # nothing to export before the first update
         g.esdf_export()
