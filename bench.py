@@ -492,8 +492,22 @@ def main():
         forms["fp32_batched_speedup_vs_one_frame"] = ms1 / ms
         forms["fp16_batched_speedup_vs_one_frame"] = ms1 / ms2
         # configs 4 and 5 at their stated sizes
+        # one persistent launch per 32-frame sub-batch instead of two
+        mf = gt.TsdfMap(w.voxel_size, w.truncation_voxels, w.max_weight, launch_mode=gt.LAUNCH_FUSED)
+        sf = make_step(mf, args.batch)
+        for _ in range(args.warmup):
+            sf()
+        msf = timed(sf, args.steps)
+        assert mf.stats()["voxel_updates"] == updates_per_step
+        forms[f"fp32_fused_{args.batch}"] = {
+            "ms_per_step": msf, "voxel_updates_per_s": ws * updates_per_step / (msf * 1e-3),
+            "frames_per_s": ws * n_frames / (msf * 1e-3),
+            "launch": "one cooperative launch per 32-frame sub-batch, sub-batches in sequence"}
+        mf.close()
         if not args.no_rig:
             forms["rig_fp16"] = rig_form(args, torch, storage=gt.STORAGE_FP16)
+            forms["rig_fp16_fused"] = rig_form(args, torch, storage=gt.STORAGE_FP16,
+                                               launch_mode=gt.LAUNCH_FUSED)
             forms["rig_fixed16"] = rig_form(args, torch, storage=gt.STORAGE_FIXED16)
         if not args.no_serving:
             forms["serving_fp16"] = serving_form(args, torch, storage=gt.STORAGE_FP16)
@@ -596,7 +610,7 @@ def _block_bytes(storage: int) -> int:
     return 512 * (8 if storage == 0 else 4)
 
 
-def rig_form(args, torch, storage: int = 1, graph_reps: int = 10) -> dict:
+def rig_form(args, torch, storage: int = 1, graph_reps: int = 10, launch_mode: int = 0) -> dict:
     """Rig workload (one outdoor map at 0.05 m; per step four pinhole frames
     of 640x480 x2, 848x480, 1280x720 and one 1024x64 LiDAR scan in one
     integrate_batch call).  The whole sequence is captured once in a CUDA
@@ -615,7 +629,8 @@ def rig_form(args, torch, storage: int = 1, graph_reps: int = 10) -> dict:
     def make(cfg):
         m = gt.TsdfMap(w.voxel_size, w.truncation_voxels, w.max_weight, storage=storage,
                        alloc_tile_h=cfg.get("alloc_tile_h", 0),
-                       integrate_ctas_per_sm=cfg.get("integrate_ctas_per_sm", 0))
+                       integrate_ctas_per_sm=cfg.get("integrate_ctas_per_sm", 0),
+                       launch_mode=launch_mode)
         descs = [gt.frame_desc(0, w.frames[i].sensor, w.frames[i].T, dev[i]) for i in range(n)]
 
         def run():
@@ -637,7 +652,9 @@ def rig_form(args, torch, storage: int = 1, graph_reps: int = 10) -> dict:
         return e0.elapsed_time(e1)
 
     cands = [{"alloc_tile_h": t, "integrate_ctas_per_sm": c} for t in (16, 32) for c in (0, 4, 6)]
-    best, timings = autotune(f"rig{args.rig_steps}s{storage}", time_cfg, cands, cache=False)
+    if launch_mode:  # one launch per step: only the tile height applies
+        cands = [{"alloc_tile_h": t} for t in (16, 32)]
+    best, timings = autotune(f"rig{args.rig_steps}s{storage}m{launch_mode}", time_cfg, cands, cache=False)
     m, run, descs = make(best)
     for _ in range(3):
         run()
@@ -685,6 +702,7 @@ def rig_form(args, torch, storage: int = 1, graph_reps: int = 10) -> dict:
     bytes_launch = ((2 * st["block_visits"] - st["blocks"]) * _block_bytes(storage) + in_bytes) / launches
     return {
         "storage": {0: "fp32", 1: "fp16", 2: "fixed16"}[storage],
+        "launch": "fused: one launch per step" if launch_mode else "split: two launches per step",
         "ms_per_sequence": ms, "steps": len(steps), "frames": n,
         "voxel_updates_per_sequence": updates,
         "voxel_updates_per_s": updates / (ms * 1e-3), "frames_per_s": n / (ms * 1e-3),

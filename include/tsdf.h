@@ -124,7 +124,17 @@ enum { TSDF_SENSOR_PINHOLE = 0, TSDF_SENSOR_LIDAR = 1 };
  * integrate_ctas_per_sm is the integration kernel's resident CTAs per SM
  * (0 = as many as fit).  For integrate_batch the first map's knobs apply.
  * layer selects the update functor (all maps of one integrate_batch call
- * must share layer and storage). */
+ * must share layer and storage).  launch_mode: TSDF_LAUNCH_SPLIT (default)
+ * runs each sub-batch of integrate_batch as an allocation launch and an
+ * integration launch, overlapping one sub-batch's allocation with the
+ * previous one's integration; TSDF_LAUNCH_FUSED runs each sub-batch as one
+ * persistent, cooperative launch that allocates, waits at a bounded
+ * grid-wide barrier (TSDF_ERR_TIMEOUT if it does not complete within about
+ * a second) and integrates, sub-batches one after the other; it covers
+ * single-map calls of TSDF layers with constant weighting and walk
+ * statistics off, and other calls fall back to the split form.  Results do
+ * not depend on the mode. */
+enum { TSDF_LAUNCH_SPLIT = 0, TSDF_LAUNCH_FUSED = 1 };
 typedef struct {
   int32_t storage;
   int64_t max_blocks;
@@ -137,6 +147,7 @@ typedef struct {
   float l_occ, l_free; /* occupancy: log-odds added per update (0, 0: 0.85, -0.4) */
   int32_t weighting;   /* TSDF weight f_w, TSDF_WEIGHT_* flags (0 = constant 1) */
   float dropoff;       /* drop-off start behind the surface, m (<= 0: one voxel) */
+  int32_t launch_mode; /* TSDF_LAUNCH_SPLIT or TSDF_LAUNCH_FUSED */
 } tsdf_map_opts;
 
 /* One frame of a batch.  `map` indexes the maps array of integrate_batch;
@@ -298,7 +309,8 @@ tsdf_status map_timing(tsdf_map* map, int32_t enable);
 
 /* map_kernel_times — waits for the recorded calls and returns the summed
  * device time of their allocation (out_ms[0]) and integration (out_ms[1])
- * kernels and the number of calls recorded; then clears the record. */
+ * kernels and the number of calls recorded; then clears the record.  A fused
+ * launch (TSDF_LAUNCH_FUSED) counts whole as allocation time. */
 tsdf_status map_kernel_times(tsdf_map* map, double out_ms[2], int64_t* calls);
 
 /*
@@ -421,6 +433,14 @@ tsdf_status map_esdf_stats(const tsdf_map* map, int64_t out[4]);
 tsdf_status map_mesh(tsdf_map* map, float min_weight, int32_t changed_only, float* tri_pos_dev,
                      int32_t* tri_keys_dev, int32_t* tri_cube_dev, int64_t cap, int64_t* n_tris,
                      void* cuda_stream);
+
+/* map_wait_test — test hook for the bounded wait of TSDF_LAUNCH_FUSED:
+ * while extra_ctas > 0, the map's fused launches wait at their grid-wide
+ * barrier for extra_ctas more CTAs than they have, so the wait runs out
+ * after about a second, the launch skips its integration and the map
+ * reports TSDF_ERR_TIMEOUT (cleared by map_reset).  0 restores normal
+ * operation.  TSDF_ERR_ARG for a negative count. */
+tsdf_status map_wait_test(tsdf_map* map, int32_t extra_ctas);
 
 /* map_reset — drop every block (keeps the allocation), enqueued on
  * cuda_stream; clears the sticky status. */

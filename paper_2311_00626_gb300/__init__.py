@@ -26,7 +26,8 @@ __all__ = ["TsdfError", "Pinhole", "Lidar", "MapOpts", "FrameDesc", "TsdfMap", "
            "integrate_color", "query_color", "map_export_color", "map_decay_occupancy",
            "EsdfOpts", "map_import", "map_esdf_update", "map_esdf_export", "map_esdf_query",
            "map_esdf_stats", "map_walk_stats", "map_mesh", "integrate_batch_host", "frame_desc_host",
-           "SENSOR_PINHOLE", "SENSOR_LIDAR", "EXPORTED_SYMBOLS"]
+           "SENSOR_PINHOLE", "SENSOR_LIDAR", "EXPORTED_SYMBOLS", "LAUNCH_SPLIT", "LAUNCH_FUSED",
+           "map_wait_test"]
 
 STORAGE_FP32, STORAGE_FP16, STORAGE_FIXED16 = 0, 1, 2
 LAYER_TSDF, LAYER_OCCUPANCY, LAYER_COLOR = 0, 1, 2
@@ -35,6 +36,7 @@ STATIC_MAX_BLOCKS = 1 << 16  # TSDF_STATIC_MAX_BLOCKS
 NUM_COUNTERS = 8  # TSDF_NUM_COUNTERS: u64 words of a caller-owned counters buffer
 KEY_BITS, KEY_BIAS = 21, 1 << 20  # TSDF_KEY_BITS, TSDF_KEY_BIAS
 SENSOR_PINHOLE, SENSOR_LIDAR = 0, 1
+LAUNCH_SPLIT, LAUNCH_FUSED = 0, 1
 _STATUS = {0: "TSDF_OK", -1: "TSDF_ERR_ARG", -2: "TSDF_ERR_CUDA", -3: "TSDF_ERR_CAPACITY",
            -4: "TSDF_ERR_TIMEOUT", -5: "TSDF_ERR_STATE"}
 EXPORTED_SYMBOLS = ["map_create", "map_create_ex", "integrate_depth", "integrate_lidar",
@@ -43,7 +45,7 @@ EXPORTED_SYMBOLS = ["map_create", "map_create_ex", "integrate_depth", "integrate
                     "integrate_depth_static", "integrate_color", "query_color",
                     "map_export_color", "map_decay_occupancy", "map_import", "map_esdf_update",
                     "map_esdf_export", "map_esdf_query", "map_esdf_stats", "map_walk_stats",
-                    "map_mesh", "integrate_batch_host", "stage_frames"]
+                    "map_mesh", "integrate_batch_host", "stage_frames", "map_wait_test"]
 
 
 class TsdfError(RuntimeError):
@@ -70,7 +72,8 @@ class MapOpts(ctypes.Structure):
                 ("lidar_guard", ctypes.c_float), ("alloc_tile_h", ctypes.c_int32),
                 ("integrate_ctas_per_sm", ctypes.c_int32), ("layer", ctypes.c_int32),
                 ("l_occ", ctypes.c_float), ("l_free", ctypes.c_float),
-                ("weighting", ctypes.c_int32), ("dropoff", ctypes.c_float)]
+                ("weighting", ctypes.c_int32), ("dropoff", ctypes.c_float),
+                ("launch_mode", ctypes.c_int32)]
 
 
 class FrameDesc(ctypes.Structure):
@@ -124,6 +127,7 @@ def lib():
                 "map_destroy": ([P], I),
                 "map_timing": ([P, I], I),
                 "map_walk_stats": ([P, I], I),
+                "map_wait_test": ([P, I], I),
                 "map_mesh": ([P, F, I, P, P, P, L64, ctypes.POINTER(ctypes.c_int64), P], I),
                 "map_kernel_times": ([P, P, ctypes.POINTER(ctypes.c_int64)], I),
                 "integrate_depth_static": ([ctypes.POINTER(MapBuffers), F, I, F, P,
@@ -215,10 +219,10 @@ def map_create(voxel_size: float, truncation_voxels: int, max_weight: float) -> 
 def map_create_ex(voxel_size, truncation_voxels, max_weight, storage=STORAGE_FP32, max_blocks=0,
                   hash_capacity=0, lidar_nearest=False, lidar_guard=0.0, alloc_tile_h=0,
                   integrate_ctas_per_sm=0, layer=LAYER_TSDF, l_occ=0.0, l_free=0.0,
-                  weighting=WEIGHT_CONSTANT, dropoff=0.0) -> int:
+                  weighting=WEIGHT_CONSTANT, dropoff=0.0, launch_mode=LAUNCH_SPLIT) -> int:
     h = ctypes.c_void_p()
     o = MapOpts(storage, max_blocks, hash_capacity, int(lidar_nearest), lidar_guard, alloc_tile_h,
-                integrate_ctas_per_sm, layer, l_occ, l_free, weighting, dropoff)
+                integrate_ctas_per_sm, layer, l_occ, l_free, weighting, dropoff, launch_mode)
     _check(lib().map_create_ex(voxel_size, truncation_voxels, max_weight, ctypes.byref(o),
                                ctypes.byref(h)), "map_create_ex")
     return h.value
@@ -305,6 +309,12 @@ def map_stats(m: int) -> dict:
 def map_walk_stats(m: int, enable: bool = True):
     """Count band segments and walked cells (map_stats "segments", "cells")."""
     _check(lib().map_walk_stats(m, int(enable)), "map_walk_stats")
+
+
+def map_wait_test(m: int, extra_ctas: int):
+    """Test hook: fused launches wait for extra_ctas CTAs that do not exist
+    (their bounded wait runs out: TSDF_ERR_TIMEOUT); 0 restores them."""
+    _check(lib().map_wait_test(m, int(extra_ctas)), "map_wait_test")
 
 
 def map_timing(m: int, enable: bool = True):
@@ -435,11 +445,12 @@ class TsdfMap:
                  storage: int = STORAGE_FP32, max_blocks: int = 0, hash_capacity: int = 0,
                  lidar_nearest: bool = False, lidar_guard: float = 0.0, alloc_tile_h: int = 0,
                  integrate_ctas_per_sm: int = 0, layer: int = LAYER_TSDF, l_occ: float = 0.0,
-                 l_free: float = 0.0, weighting: int = WEIGHT_CONSTANT, dropoff: float = 0.0):
+                 l_free: float = 0.0, weighting: int = WEIGHT_CONSTANT, dropoff: float = 0.0,
+                 launch_mode: int = LAUNCH_SPLIT):
         self.handle = map_create_ex(voxel_size, truncation_voxels, max_weight, storage,
                                     max_blocks, hash_capacity, lidar_nearest, lidar_guard,
                                     alloc_tile_h, integrate_ctas_per_sm, layer, l_occ, l_free,
-                                    weighting, dropoff)
+                                    weighting, dropoff, launch_mode)
         self.voxel_size = voxel_size
         self.storage = storage
 

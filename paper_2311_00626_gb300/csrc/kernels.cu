@@ -218,30 +218,34 @@ __device__ __forceinline__ bool pixel_segment(const FrameDev& F, const MapDev& m
   return valid;
 }
 
-// One CTA per kTileW x TH pixel tile of one frame.  Each warp walks the
-// band segments of one pixel row at a time and records the blocks met in a
-// CTA-local set; then the tile's distinct blocks are claimed in the global
-// hash.  Segments that start far from the sensor's block count cells from
-// their own start cell and claim their blocks directly.  PINHOLE_ONLY: every
-// frame of the batch is a pinhole camera (the LiDAR code is left out);
-// STATS: count band segments and walked cells (a diagnostic, 5 % slower).
+// Shared memory of one allocation tile.
+template <int TH>
+struct AllocSmem {
+  uint32_t set[kSetSize];   // CTA-local set of relative block keys
+  uint32_t keys[kSetSize];  // the set's keys, compacted
+  uint32_t nkeys;
+  float ray[kTileW + TH];   // pinhole: (i - cu) / fu per column, (j - cv) / fv per row
+};
+
+// Allocation tile `cta` of the batch (tiles are numbered frame by frame,
+// FrameDev::blk_begin being a frame's first), run by all kAllocThreads
+// threads of a CTA.  With p.overlap the stream's next kernel may be
+// scheduled once the walks are done.
 template <int NF, int NM, int TH, bool PINHOLE_ONLY, bool STATS>
-__global__ void __launch_bounds__(kAllocThreads)
-    band_alloc_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
+__device__ __forceinline__ void alloc_tile(const BatchParams<NF, NM>& p, int cta, AllocSmem<TH>& sm) {
   constexpr int kRows = TH * kTileW / kAllocThreads;  // pixel rows per thread
-  if (p.overlap) wait_prev_grid();
   uint32_t segs = 0, cells = 0;                        // walk statistics
-  __shared__ uint32_t s_set[kSetSize];
-  __shared__ uint32_t s_keys[kSetSize];
-  __shared__ uint32_t s_nkeys;
-  __shared__ float s_ray[kTileW + TH];  // pinhole: (i - cu) / fu per column, (j - cv) / fv per row
+  uint32_t* s_set = sm.set;
+  uint32_t* s_keys = sm.keys;
+  float* s_ray = sm.ray;
+  __syncthreads();  // a previous tile of this CTA is done with the shared arrays
   for (int i = threadIdx.x; i < kSetSize; i += kAllocThreads) s_set[i] = kEmptyRel;
-  if (threadIdx.x == 0) s_nkeys = 0;
-  // frame of this CTA: the last frame whose first tile is <= blockIdx.x
+  if (threadIdx.x == 0) sm.nkeys = 0;
+  // frame of this tile: the last frame whose first tile is <= cta
   int f = 0;
   for (int lo = 1, hi = p.n_frames - 1; lo <= hi;) {
     const int mid = (lo + hi) >> 1;
-    if ((int)blockIdx.x >= p.fr[mid].blk_begin) {
+    if (cta >= p.fr[mid].blk_begin) {
       f = mid;
       lo = mid + 1;
     } else {
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(kAllocThreads)
   // with one map its fields are constant operands, not indexed loads
   const MapDev& m = NM == 1 ? p.maps[0] : p.maps[F.map];
   const int tiles_x = (F.width + kTileW - 1) / kTileW;
-  const int tile = (int)blockIdx.x - F.blk_begin;
+  const int tile = cta - F.blk_begin;
   const int x0 = (tile % tiles_x) * kTileW, y0 = (tile / tiles_x) * TH;
   const int lane = threadIdx.x % kTileW, wy = threadIdx.x / kTileW;
   // all of this thread's depths are requested before any is used
@@ -311,10 +315,10 @@ __global__ void __launch_bounds__(kAllocThreads)
   // compact the tile's distinct blocks, then claim them one per thread
   for (int i = threadIdx.x; i < kSetSize; i += kAllocThreads) {
     const uint32_t key = s_set[i];
-    if (key != kEmptyRel) s_keys[atomicAdd(&s_nkeys, 1u)] = key;
+    if (key != kEmptyRel) s_keys[atomicAdd(&sm.nkeys, 1u)] = key;
   }
   __syncthreads();
-  const uint32_t nk = s_nkeys;
+  const uint32_t nk = sm.nkeys;
   for (uint32_t i = threadIdx.x; i < nk; i += kAllocThreads) claim_block(m, rel_to_key(s_keys[i], F.a), F.bit);
   if (STATS) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -326,6 +330,21 @@ __global__ void __launch_bounds__(kAllocThreads)
       atomicAdd(m.counters + kCntCells, (unsigned long long)cells);
     }
   }
+}
+
+// One CTA per kTileW x TH pixel tile of one frame.  Each warp walks the
+// band segments of one pixel row at a time and records the blocks met in a
+// CTA-local set; then the tile's distinct blocks are claimed in the global
+// hash.  Segments that start far from the sensor's block count cells from
+// their own start cell and claim their blocks directly.  PINHOLE_ONLY: every
+// frame of the batch is a pinhole camera (the LiDAR code is left out);
+// STATS: count band segments and walked cells (a diagnostic, 5 % slower).
+template <int NF, int NM, int TH, bool PINHOLE_ONLY, bool STATS>
+__global__ void __launch_bounds__(kAllocThreads)
+    band_alloc_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
+  if (p.overlap) wait_prev_grid();
+  __shared__ AllocSmem<TH> sm;
+  alloc_tile<NF, NM, TH, PINHOLE_ONLY, STATS>(p, (int)blockIdx.x, sm);
 }
 
 // ------------------------------------------------ per-voxel projection
@@ -725,59 +744,91 @@ __device__ __forceinline__ void fuse_lidar(const FrameDev& F, const MapDev& m, c
   }
 }
 
-template <int NF, int NM, int STORAGE, bool PINHOLE_ONLY, bool WEIGHTED>
-__global__ void __launch_bounds__(kIntegrateThreads)
-    integrate_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
-  __shared__ uint32_t s_begin[NM + 1];
-  __shared__ unsigned long long s_upd[NM];
-  __shared__ unsigned long long s_pairs[NM];
-  __shared__ uint32_t s_next[2];
-  __shared__ FrameProj s_fp[NF];
-  if (p.overlap) wait_prev_grid();
-  const int t = threadIdx.x;
-  if (t < NM) s_upd[t] = s_pairs[t] = 0ull;
-  for (int f = t; f < p.n_frames; f += kIntegrateThreads)
-    if (p.fr[f].kind == kSensorPinhole) stage_frame(p.fr[f], s_fp[f]);
-  if (t == 0) s_next[0] = blockIdx.x;
-  if (t == 0) {
+// Shared memory of the integration workers of a CTA: G groups of
+// kIntegrateThreads threads, each group working on its own work-list
+// entries.
+template <int NF, int NM, int G>
+struct IntegSmem {
+  uint32_t begin[NM + 1];         // first entry of each map's list in the batch's work
+  unsigned long long upd[NM];     // voxel updates per map
+  unsigned long long pairs[NM];   // (block, frame) pairs per map
+  uint32_t next[G][2];            // per group: the entry in hand and the next one
+  FrameProj fp[NF];
+};
+
+// Barrier of the kIntegrateThreads threads of worker group g: the CTA
+// barrier when the CTA is one group, else hardware barrier 1 + g.
+template <int G>
+__device__ __forceinline__ void group_sync(int g) {
+  if (G == 1) {
+    __syncthreads();
+  } else if (g == 0) {
+    asm volatile("bar.sync 1, %0;" ::"n"(kIntegrateThreads) : "memory");
+  } else {
+    asm volatile("bar.sync 2, %0;" ::"n"(kIntegrateThreads) : "memory");
+  }
+}
+
+// Entry metadata: COHERENT loads bypass L1, for a kernel that reads
+// metadata that other CTAs of the same launch wrote.
+template <bool COHERENT, class T>
+__device__ __forceinline__ T meta_load(const T* a) {
+  if (COHERENT) return __ldcg(a);
+  return *a;
+}
+
+// The integration of a batch's work list: every entry is a hash slot met by
+// some frames of the batch; its block's 512 voxels are held in registers (4
+// per thread) across those frames, in batch order, and written back once.
+// Entries are handed out dynamically (blocks differ in their frame counts);
+// next[g] is double-buffered so one group barrier per entry suffices.  The
+// last CTA to finish resets every map's work list for the next batch.
+template <int NF, int NM, int G, bool COHERENT, int STORAGE, bool PINHOLE_ONLY, bool WEIGHTED>
+__device__ __forceinline__ void integrate_entries(const BatchParams<NF, NM>& p, IntegSmem<NF, NM, G>& sm) {
+  static_assert(G == 1 || G == 2, "one or two worker groups per CTA");
+  const int g = G == 1 ? 0 : (int)threadIdx.x / kIntegrateThreads;
+  const int t = G == 1 ? (int)threadIdx.x : (int)threadIdx.x % kIntegrateThreads;
+  if (threadIdx.x < NM) sm.upd[threadIdx.x] = sm.pairs[threadIdx.x] = 0ull;
+  for (int f = threadIdx.x; f < p.n_frames; f += G * kIntegrateThreads)
+    if (p.fr[f].kind == kSensorPinhole) stage_frame(p.fr[f], sm.fp[f]);
+  if (t == 0) sm.next[g][0] = blockIdx.x * G + g;
+  if (threadIdx.x == 0) {
     // the batch's work = the concatenation of every map's list
     uint32_t acc = 0;
     for (int k = 0; k < p.n_maps; ++k) {
-      s_begin[k] = acc;
+      sm.begin[k] = acc;
       acc += min(__ldcg(p.maps[k].ctl), p.maps[k].list_cap);
     }
-    s_begin[p.n_maps] = acc;
+    sm.begin[p.n_maps] = acc;
   }
   __syncthreads();
-  const uint32_t n = s_begin[p.n_maps];
+  const uint32_t n = sm.begin[p.n_maps];
   // this thread's voxels: x = lx0 .. lx0 + 3 at (ly, lz)
   const int lx0 = (t & 1) * 4, ly = (t >> 1) & 7, lz = t >> 4;
 
-  // entries are handed out dynamically (blocks differ in their frame
-  // counts); s_next is double-buffered so one barrier per entry suffices
   for (uint32_t it = 0;; ++it) {
-    const uint32_t e = s_next[it & 1u];
+    const uint32_t e = sm.next[g][it & 1u];
     if (e >= n) break;
-    if (t == 0) s_next[(it + 1) & 1u] = gridDim.x + atomicAdd(p.maps[0].ctl + 2, 1u);
+    if (t == 0) sm.next[g][(it + 1) & 1u] = gridDim.x * G + atomicAdd(p.maps[0].ctl + 2, 1u);
     // every thread reads the entry's metadata itself (same addresses across
-    // the CTA), so no warp waits on another before its voxel loads
+    // the group), so no warp waits on another before its voxel loads
     int mi = 0;
-    while (mi + 1 < p.n_maps && e >= s_begin[mi + 1]) ++mi;
+    while (mi + 1 < p.n_maps && e >= sm.begin[mi + 1]) ++mi;
     const MapDev& m = NM == 1 ? p.maps[0] : p.maps[mi];
-    const uint32_t slot = m.list[e - s_begin[mi]];
-    const int val = m.vals[slot];
-    const uint32_t slot_mask = m.mask[slot];
-    const unsigned long long slot_key = m.keys[slot];
+    const uint32_t slot = meta_load<COHERENT>(m.list + (e - sm.begin[mi]));
+    const int val = meta_load<COHERENT>(m.vals + slot);
+    const uint32_t slot_mask = meta_load<COHERENT>(m.mask + slot);
+    const unsigned long long slot_key = meta_load<COHERENT>(m.keys + slot);
     const bool fresh = val <= -2;
     const int pool = fresh ? -val - 2 : val;
     unsigned long long my_upd = 0;
     if (val != -1) {
-      float D[4], W[4], G[4], B[4];
+      float D[4], W[4], G4[4], B[4];
       if (fresh) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) { D[i] = 0.0f; W[i] = 0.0f; G[i] = 0.0f; B[i] = 0.0f; }
+        for (int i = 0; i < 4; ++i) { D[i] = 0.0f; W[i] = 0.0f; G4[i] = 0.0f; B[i] = 0.0f; }
       } else {
-        Voxels4<STORAGE>::load(m, pool, t, D, W, G, B);
+        Voxels4<STORAGE>::load(m, pool, t, D, W, G4, B);
       }
       const int bx = key_coord(slot_key, 0), by = key_coord(slot_key, 1), bz = key_coord(slot_key, 2);
       const VoxelRow vr{bx, by, bz, lx0, ly, lz};
@@ -805,22 +856,22 @@ __global__ void __launch_bounds__(kIntegrateThreads)
           }
         }
         fq[2] = fq[3] = -1;
-        if (nq == 2) fuse_pinhole<2, STORAGE, WEIGHTED>(p, s_fp, fq, m, vr, D, W, G, B, my_upd);
-        else if (nq == 1) fuse_pinhole<1, STORAGE, WEIGHTED>(p, s_fp, fq, m, vr, D, W, G, B, my_upd);
+        if (nq == 2) fuse_pinhole<2, STORAGE, WEIGHTED>(p, sm.fp, fq, m, vr, D, W, G4, B, my_upd);
+        else if (nq == 1) fuse_pinhole<1, STORAGE, WEIGHTED>(p, sm.fp, fq, m, vr, D, W, G4, B, my_upd);
         else if (!PINHOLE_ONLY) {
           const int f = __ffs(bits) - 1;  // a LiDAR frame
           bits &= bits - 1u;
           fuse_lidar<STORAGE, WEIGHTED>(p.fr[f], m, vr, D, W, my_upd);
         }
       }
-      Voxels4<STORAGE>::store(m, pool, t, D, W, G, B);
+      Voxels4<STORAGE>::store(m, pool, t, D, W, G4, B);
     }
     // per-map update count: warp sums into a shared per-map counter
     for (int o = 16; o > 0; o >>= 1) my_upd += __shfl_down_sync(0xffffffffu, my_upd, o);
-    if ((t & 31) == 0 && my_upd) atomicAdd(&s_upd[mi], my_upd);
-    __syncthreads();  // every warp has read this entry's metadata
+    if ((t & 31) == 0 && my_upd) atomicAdd(&sm.upd[mi], my_upd);
+    group_sync<G>(g);  // every warp of the group has read this entry's metadata
     if (t == 0) {
-      atomicAdd(&s_pairs[mi], (unsigned long long)__popc(slot_mask));
+      atomicAdd(&sm.pairs[mi], (unsigned long long)__popc(slot_mask));
       m.mask[slot] = 0u;
       if (fresh) m.vals[slot] = pool;
       if (m.dirty && val != -1) m.dirty[pool] = kDirtyEsdf | kDirtyMesh;
@@ -828,22 +879,105 @@ __global__ void __launch_bounds__(kIntegrateThreads)
   }
   if (p.overlap) allow_next_grid();
   __syncthreads();
-  if (t < p.n_maps && s_upd[t]) atomicAdd(p.maps[t].counters + kCntUpdates, s_upd[t]);
-  if (t < p.n_maps && s_pairs[t]) atomicAdd(p.maps[t].counters + kCntPairs, s_pairs[t]);
+  if (threadIdx.x < p.n_maps && sm.upd[threadIdx.x])
+    atomicAdd(p.maps[threadIdx.x].counters + kCntUpdates, sm.upd[threadIdx.x]);
+  if (threadIdx.x < p.n_maps && sm.pairs[threadIdx.x])
+    atomicAdd(p.maps[threadIdx.x].counters + kCntPairs, sm.pairs[threadIdx.x]);
   // the last CTA to finish resets every map's work list for the next batch
-  if (t == 0) {
+  if (threadIdx.x == 0) {
     __threadfence();
     const unsigned done = atomicAdd(p.maps[0].ctl + 1, 1u);
     if (done == gridDim.x - 1) {
       for (int k = 0; k < p.n_maps; ++k) {
-        atomicAdd(p.maps[k].counters + kCntVisits, (unsigned long long)(s_begin[k + 1] - s_begin[k]));
+        atomicAdd(p.maps[k].counters + kCntVisits, (unsigned long long)(sm.begin[k + 1] - sm.begin[k]));
         atomicAdd(p.maps[k].counters + kCntLaunches, 1ull);
         p.maps[k].ctl[0] = 0u;
       }
       p.maps[0].ctl[1] = 0u;
       p.maps[0].ctl[2] = 0u;
+      p.maps[0].ctl[3] = 0u;  // the fused kernel's barrier count
     }
   }
+}
+
+template <int NF, int NM, int STORAGE, bool PINHOLE_ONLY, bool WEIGHTED>
+__global__ void __launch_bounds__(kIntegrateThreads)
+    integrate_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
+  __shared__ IntegSmem<NF, NM, 1> sm;
+  if (p.overlap) wait_prev_grid();
+  integrate_entries<NF, NM, 1, false, STORAGE, PINHOLE_ONLY, WEIGHTED>(p, sm);
+}
+
+// ------------------------------------------- one launch per batch (fused)
+
+// Bounded waits give up after this many nanoseconds of the global timer.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned int load_acquire(const unsigned int* a) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs resident): thread 0 of
+// every CTA arrives on *count, then waits until `expected` CTAs have arrived,
+// for at most kWaitLimitNs.  A wait that runs out sets kStTimeout in *status
+// (the map's sticky status) and makes the CTA return false.
+__device__ __noinline__ bool grid_wait(unsigned int* count, unsigned int expected, unsigned long long* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    const unsigned long long t0 = global_ns();
+    int ok = 1;
+    while (load_acquire(count) < expected) {
+      if (global_ns() - t0 > kWaitLimitNs) {
+        atomicOr(status, (unsigned long long)kStTimeout);
+        ok = 0;
+        break;
+      }
+      __nanosleep(128);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+constexpr int kFusedThreads = kAllocThreads;  // two integration worker groups
+static_assert(kFusedThreads == 2 * kIntegrateThreads, "fused CTA = two integration groups");
+
+template <int NF, int NM, int TH>
+union FusedSmem {
+  AllocSmem<TH> a;
+  IntegSmem<NF, NM, 2> i;
+};
+
+// Allocation and integration of one batch in one persistent, cooperative
+// launch: the CTAs walk every allocation tile of the batch (grid-stride),
+// meet at a bounded grid-wide wait (the integration reads the work list,
+// slot masks and pool indices that every tile wrote), then integrate the
+// work list as two groups of kIntegrateThreads per CTA.  Single-map
+// batches, TSDF storage, constant weighting, no walk statistics.
+// Four resident CTAs per SM (64 registers): the rig's fused step measured
+// 16.1 ms per 1,000 frames against 18.2 ms with three.
+template <int NF, int NM, int TH, int STORAGE, bool PINHOLE_ONLY>
+__global__ void __launch_bounds__(kFusedThreads, 4)
+    fused_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
+  __shared__ FusedSmem<NF, NM, TH> sm;
+  for (int cta = blockIdx.x; cta < p.alloc_ctas; cta += gridDim.x)
+    alloc_tile<NF, NM, TH, PINHOLE_ONLY, false>(p, cta, sm.a);
+  if (!grid_wait(p.maps[0].ctl + 3, gridDim.x + (unsigned)p.wait_extra, p.maps[0].counters + kCntStatus))
+    return;  // timed out: integration skipped, the map reports TSDF_ERR_TIMEOUT
+  integrate_entries<NF, NM, 2, true, STORAGE, PINHOLE_ONLY, false>(p, sm.i);
 }
 
 template <int STORAGE>
@@ -1033,6 +1167,59 @@ cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStrea
     return launch_k(integrate_kernel<NF, NM, kStorageF32, false, false>, g, b, s, p);
 }
 
+// The fused kernel of a tile height for a storage and sensor mix, launched
+// cooperatively with as many CTAs as can be resident at once.
+template <int NF, int NM, int TH>
+cudaError_t launch_fused_th(const BatchParams<NF, NM>& p, int st, bool ph, cudaStream_t s) {
+  void (*k)(BatchParams<NF, NM>) = nullptr;
+  int si = 0;
+  if (st == kStorageF32) {
+    k = ph ? fused_kernel<NF, NM, TH, kStorageF32, true> : fused_kernel<NF, NM, TH, kStorageF32, false>;
+    si = 0;
+  } else if (st == kStorageF16) {
+    k = ph ? fused_kernel<NF, NM, TH, kStorageF16, true> : fused_kernel<NF, NM, TH, kStorageF16, false>;
+    si = 1;
+  } else {
+    k = ph ? fused_kernel<NF, NM, TH, kStorageX16, true> : fused_kernel<NF, NM, TH, kStorageX16, false>;
+    si = 2;
+  }
+  static int per_sm[3][2] = {};  // resident CTAs per SM of each variant (all devices are alike here)
+  int& n = per_sm[si][ph ? 1 : 0];
+  if (n == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kFusedThreads, 0) != cudaSuccess) {
+    n = 0;
+    return cudaGetLastError();
+  }
+  if (n <= 0) return cudaErrorNotSupported;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n * sms);
+  cfg.blockDim = dim3(kFusedThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the grid-wide wait can complete
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, p);
+}
+
+template <int NF, int NM>
+cudaError_t launch_fused(const BatchParams<NF, NM>& p, int tile_h, cudaStream_t s) {
+  const MapDev& m0 = p.maps[0];
+  if (NM != 1 || p.n_maps != 1 || p.overlap || m0.walk_stats || m0.weighting != 0) return cudaErrorNotSupported;
+  const int st = m0.storage;
+  if (st != kStorageF32 && st != kStorageF16 && st != kStorageX16) return cudaErrorNotSupported;
+  if (p.alloc_ctas <= 0) return cudaErrorNotSupported;
+  const bool ph = pinhole_only(p);
+  return tile_h == kTileHBig ? launch_fused_th<NF, NM, kTileHBig>(p, st, ph, s)
+                             : launch_fused_th<NF, NM, kTileHSmall>(p, st, ph, s);
+}
+
+template cudaError_t launch_fused<kMaxFrames, 1>(const BatchParams<kMaxFrames, 1>&, int, cudaStream_t);
 template cudaError_t launch_band_alloc<1, 1>(const BatchParams<1, 1>&, int, int, cudaStream_t);
 template cudaError_t launch_band_alloc<kMaxFrames, kMaxMaps>(const BatchParams<kMaxFrames, kMaxMaps>&,
                                                              int, int, cudaStream_t);

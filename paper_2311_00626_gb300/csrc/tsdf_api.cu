@@ -37,6 +37,8 @@ struct tsdf_map {
   double vd, Bd;
   int n_ctas_integrate;
   int tile_h;  // allocation tile height, 0 = automatic
+  int launch_mode;     // TSDF_LAUNCH_SPLIT or TSDF_LAUNCH_FUSED
+  int32_t wait_extra;  // map_wait_test: extra CTAs the fused launch's grid-wide wait expects
   int64_t frames;
   unsigned long long status_seen;  // device status bits observed by the host
   std::vector<LidarTable> tables;
@@ -368,6 +370,7 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   if (o.alloc_tile_h != 0 && o.alloc_tile_h != gbt::kTileHSmall && o.alloc_tile_h != gbt::kTileHBig)
     return TSDF_ERR_ARG;
   if (o.integrate_ctas_per_sm < 0) return TSDF_ERR_ARG;
+  if (o.launch_mode != TSDF_LAUNCH_SPLIT && o.launch_mode != TSDF_LAUNCH_FUSED) return TSDF_ERR_ARG;
   if (o.storage != TSDF_STORAGE_FP32 && o.storage != TSDF_STORAGE_FP16 && o.storage != TSDF_STORAGE_FIXED16 &&
       o.storage != gbt::kStorageOcc && o.storage != gbt::kStorageColor)
     return TSDF_ERR_ARG;
@@ -450,6 +453,8 @@ tsdf_status map_create_ex(float voxel_size, int32_t truncation_voxels, float max
   if (o.integrate_ctas_per_sm > 0) per_sm = std::min(per_sm, o.integrate_ctas_per_sm);
   m->n_ctas_integrate = std::max(1, sms) * per_sm;
   m->tile_h = o.alloc_tile_h;
+  m->launch_mode = o.launch_mode;
+  m->wait_extra = 0;
   *out = m;
   return TSDF_OK;
 }
@@ -526,6 +531,59 @@ tsdf_status run_batch(tsdf_map* const* maps, int32_t n_maps, std::vector<FrameDe
   static thread_local BatchParams<gbt::kMaxFrames, 1> p1;
   tsdf_map* lead = maps[0];
   const int n_sub = (n + gbt::kMaxFrames - 1) / gbt::kMaxFrames;
+  if (lead->launch_mode == TSDF_LAUNCH_FUSED && n_maps == 1) {
+    // one cooperative launch per sub-batch, on the caller's stream
+    for (int b = 0; b < n_sub; ++b) {
+      const int f0 = b * gbt::kMaxFrames, nf = std::min(gbt::kMaxFrames, n - f0);
+      if (hook) {
+        tsdf_status st = hook(ctx, b, f0, nf, s);
+        if (st != TSDF_OK) return st;
+      }
+      std::memset(&p1, 0, sizeof(p1));
+      p1.n_frames = nf;
+      p1.n_maps = 1;
+      p1.maps[0] = view_set(lead, 0);
+      int64_t pixels = 0;
+      for (int f = 0; f < nf; ++f) {
+        p1.fr[f] = fr[f0 + f];
+        p1.fr[f].bit = f;
+        pixels += (int64_t)p1.fr[f].width * p1.fr[f].height;
+      }
+      const int th = lead->tile_h ? lead->tile_h : pick_tile_h(pixels);
+      int ctas = 0;
+      for (int f = 0; f < nf; ++f) {
+        p1.fr[f].blk_begin = ctas;
+        ctas += alloc_ctas(p1.fr[f], th);
+      }
+      p1.alloc_ctas = ctas;
+      p1.wait_extra = lead->wait_extra;
+      cudaEvent_t* ev = timing_slot(lead);
+      if (ev) cudaEventRecord(ev[0], s);
+      cudaError_t err = gbt::launch_fused(p1, th, s);
+      if (err == cudaErrorNotSupported) {  // not a fused batch: the two kernels
+        cudaGetLastError();
+        p1.overlap = 1;
+        if (gbt::launch_band_alloc(p1, ctas, th, s) != cudaSuccess) return cuda_fail();
+        if (ev) {
+          cudaEventRecord(ev[1], s);
+          cudaEventRecord(ev[2], s);
+        }
+        if (gbt::launch_integrate(p1, lead->n_ctas_integrate, s) != cudaSuccess) return cuda_fail();
+        if (ev) cudaEventRecord(ev[3], s);
+        if (cudaEventRecord(lead->ev_int[b & 3], s) != cudaSuccess) return cuda_fail();
+        continue;
+      }
+      if (err != cudaSuccess) return cuda_fail();
+      if (ev) {  // the whole launch counts as allocation time
+        cudaEventRecord(ev[1], s);
+        cudaEventRecord(ev[2], s);
+        cudaEventRecord(ev[3], s);
+      }
+      // host-image staging reuses this sub-batch's slot after this event
+      if (cudaEventRecord(lead->ev_int[b & 3], s) != cudaSuccess) return cuda_fail();
+    }
+    return TSDF_OK;
+  }
   const bool piped = n_sub > 1;
   if (piped && (cudaEventRecord(lead->ev_start, s) != cudaSuccess ||
                 cudaStreamWaitEvent(lead->aux, lead->ev_start, 0) != cudaSuccess))
@@ -1180,6 +1238,12 @@ tsdf_status map_mesh(tsdf_map* map, float min_weight, int32_t changed_only, floa
     return cuda_fail();
   *n_tris = (int64_t)cnt[1];
   return cnt[1] > (unsigned long long)cap ? TSDF_ERR_CAPACITY : TSDF_OK;
+}
+
+tsdf_status map_wait_test(tsdf_map* map, int32_t extra_ctas) {
+  if (!map || extra_ctas < 0) return TSDF_ERR_ARG;
+  map->wait_extra = extra_ctas;
+  return TSDF_OK;
 }
 
 tsdf_status map_reset(tsdf_map* map, void* cuda_stream) {

@@ -154,7 +154,9 @@ template <int NF, int NM>
 struct BatchParams {
   int32_t n_frames;
   int32_t n_maps;
-  int32_t overlap;  // launched as a programmatic dependent of the stream's previous kernel
+  int32_t overlap;     // launched as a programmatic dependent of the stream's previous kernel
+  int32_t alloc_ctas;  // allocation tiles of the batch (the fused kernel loops over them)
+  int32_t wait_extra;  // test hook: the fused kernel's grid wait expects this many extra CTAs
   MapDev maps[NM];
   FrameDev fr[NF];
 };
@@ -198,6 +200,11 @@ template <int NF, int NM>
 cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile_h, cudaStream_t s);
 template <int NF, int NM>
 cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStream_t s);
+// Allocation and integration of one batch in a single cooperative launch;
+// cudaErrorNotSupported for batches it does not cover (the caller then
+// launches the two kernels).
+template <int NF, int NM>
+cudaError_t launch_fused(const BatchParams<NF, NM>& p, int tile_h, cudaStream_t s);
 cudaError_t launch_query_color(const MapDev& m, const float* pts, int64_t n, float* rgb, float* weight,
                                cudaStream_t s);
 cudaError_t launch_query(const MapDev& m, const float* pts, int64_t n, float* dist, float* weight,
