@@ -41,6 +41,22 @@ __device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol
 constexpr float kPiF = (float)3.14159265358979323846;
 constexpr float kHalfPiF = (float)(3.14159265358979323846 / 2);
 
+// IEEE round-to-nearest reciprocal of a decision input.  FAST: the hardware
+// approximation (within 1 ulp) refined by one Newton step with fused
+// multiply-adds, e = 1 - x y, y' = y + y e (Markstein's method), which equals
+// __frcp_rn(x) bit for bit for |x| in [2^-126, 2^126] (checked over all
+// 4,227,858,434 such inputs).  The host selects FAST kernels only for
+// batches whose inverted values all lie in that range or are zero (zero is
+// never inverted), see fast_rcp_ok in the host code.
+template <bool FAST>
+__device__ __forceinline__ float rcp_dec(float x) {
+  if (!FAST) return __frcp_rn(x);
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  const float e = __fmaf_rn(-x, y, 1.0f);
+  return __fmaf_rn(y, e, y);
+}
+
 // ------------------------------------------------------------------ hash
 
 __device__ __forceinline__ int hash_insert(const MapDev& m, unsigned long long key, bool& inserted) {
@@ -108,15 +124,17 @@ struct Walk32 {
 
   // t of an axis is always (b - o) * inv; an axis with zero direction has
   // b = +inf and inv = 1, so its t is +inf.
+  template <bool FAST>
   __device__ __forceinline__ void axis(float d, float fl, float o, uint32_t unit, float& f,
                                        uint32_t& k, float& inv, float& b, float& t) {
     const bool pos = d > 0.0f, neg = d < 0.0f;
     f = pos ? 1.0f : (neg ? -1.0f : 0.0f);
     k = pos ? unit : (neg ? 0u - unit : 0u);
-    inv = (pos || neg) ? __frcp_rn(d) : 1.0f;
+    inv = (pos || neg) ? rcp_dec<FAST>(d) : 1.0f;
     b = pos ? fl + 1.0f : (neg ? fl : __int_as_float(0x7f800000));
     t = __fmul_rn(__fsub_rn(b, o), inv);
   }
+  template <bool FAST>
   __device__ __forceinline__ void start(float px, float py, float pz, float ox_, float oy_, float oz_,
                                         float dx, float dy, float dz, float s1_, int bx0, int by0,
                                         int bz0, uint32_t flag) {
@@ -126,9 +144,9 @@ struct Walk32 {
     const float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
     key = ((uint32_t)((int)flx - bx0 + kRelBias) | ((uint32_t)((int)fly - by0 + kRelBias) << 10) |
            ((uint32_t)((int)flz - bz0 + kRelBias) << 20)) | flag;
-    axis(dx, flx, ox, 1u, fx, kx, ix, bx, tx);
-    axis(dy, fly, oy, 1u << 10, fy, ky, iy, by, ty);
-    axis(dz, flz, oz, 1u << 20, fz, kz, iz, bz, tz);
+    axis<FAST>(dx, flx, ox, 1u, fx, kx, ix, bx, tx);
+    axis<FAST>(dy, fly, oy, 1u << 10, fy, ky, iy, by, ty);
+    axis<FAST>(dz, flz, oz, 1u << 20, fz, kz, iz, bz, tz);
     s1 = s1_;
     n = 1;
   }
@@ -231,7 +249,7 @@ struct AllocSmem {
 // FrameDev::blk_begin being a frame's first), run by all kAllocThreads
 // threads of a CTA.  With p.overlap the stream's next kernel may be
 // scheduled once the walks are done.
-template <int NF, int NM, int TH, bool PINHOLE_ONLY, bool STATS>
+template <int NF, int NM, int TH, bool PINHOLE_ONLY, bool STATS, bool FAST>
 __device__ __forceinline__ void alloc_tile(const BatchParams<NF, NM>& p, int cta, AllocSmem<TH>& sm) {
   constexpr int kRows = TH * kTileW / kAllocThreads;  // pixel rows per thread
   uint32_t segs = 0, cells = 0;                        // walk statistics
@@ -286,7 +304,7 @@ __device__ __forceinline__ void alloc_tile(const BatchParams<NF, NM>& p, int cta
       const float px = __fmaf_rn(s0, dx, F.o[0]), py = __fmaf_rn(s0, dy, F.o[1]),
                   pz = __fmaf_rn(s0, dz, F.o[2]);
       if (fabsf(px) < kRelStart && fabsf(py) < kRelStart && fabsf(pz) < kRelStart) {
-        wk.start(px, py, pz, F.o[0], F.o[1], F.o[2], dx, dy, dz, s1, 0, 0, 0, 0u);
+        wk.start<FAST>(px, py, pz, F.o[0], F.o[1], F.o[2], dx, dy, dz, s1, 0, 0, 0, 0u);
         live = true;
       } else if (fabsf(px) < 262144.0f && fabsf(py) < 262144.0f && fabsf(pz) < 262144.0f) {
         // far from the sensor's block (long range or small voxels): count
@@ -294,7 +312,7 @@ __device__ __forceinline__ void alloc_tile(const BatchParams<NF, NM>& p, int cta
         b0x = (int)floorf(px);
         b0y = (int)floorf(py);
         b0z = (int)floorf(pz);
-        wk.start(px, py, pz, F.o[0], F.o[1], F.o[2], dx, dy, dz, s1, b0x, b0y, b0z, kFarFlag);
+        wk.start<FAST>(px, py, pz, F.o[0], F.o[1], F.o[2], dx, dy, dz, s1, b0x, b0y, b0z, kFarFlag);
         live = true;
       }
     }
@@ -338,13 +356,14 @@ __device__ __forceinline__ void alloc_tile(const BatchParams<NF, NM>& p, int cta
 // hash.  Segments that start far from the sensor's block count cells from
 // their own start cell and claim their blocks directly.  PINHOLE_ONLY: every
 // frame of the batch is a pinhole camera (the LiDAR code is left out);
-// STATS: count band segments and walked cells (a diagnostic, 5 % slower).
-template <int NF, int NM, int TH, bool PINHOLE_ONLY, bool STATS>
+// STATS: count band segments and walked cells (a diagnostic, 5 % slower);
+// FAST: reciprocals by rcp_dec<true> (the host checked their range).
+template <int NF, int NM, int TH, bool PINHOLE_ONLY, bool STATS, bool FAST>
 __global__ void __launch_bounds__(kAllocThreads)
     band_alloc_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
   if (p.overlap) wait_prev_grid();
   __shared__ AllocSmem<TH> sm;
-  alloc_tile<NF, NM, TH, PINHOLE_ONLY, STATS>(p, (int)blockIdx.x, sm);
+  alloc_tile<NF, NM, TH, PINHOLE_ONLY, STATS, FAST>(p, (int)blockIdx.x, sm);
 }
 
 // ------------------------------------------------ per-voxel projection
@@ -616,7 +635,7 @@ __device__ __forceinline__ void row_points_staged(const float4& r0, const float4
 // order.  An out-of-image projection reads no pixel and yields d = 0, which
 // is invalid like a missing depth.  A colour layer updates only voxels within
 // tau of the surface on both sides.
-template <int NQ, int STORAGE, bool WEIGHTED, class P>
+template <int NQ, int STORAGE, bool WEIGHTED, bool FAST, class P>
 __device__ __forceinline__ void fuse_pinhole(const P& p, const FrameProj* s_fp, const int (&fq)[4],
                                              const MapDev& m, const VoxelRow& r, float* D, float* W,
                                              float* G, float* B, unsigned long long& upd) {
@@ -637,7 +656,7 @@ __device__ __forceinline__ void fuse_pinhole(const P& p, const FrameProj* s_fp, 
     const float2 half = make_float2(0.5f, 0.5f);
 #pragma unroll
     for (int i = 0; i < 4; i += 2) {
-      const float2 iz = make_float2(__frcp_rn(z[q][i]), __frcp_rn(z[q][i + 1]));
+      const float2 iz = make_float2(rcp_dec<FAST>(z[q][i]), rcp_dec<FAST>(z[q][i + 1]));
       const float2 u = __fadd2_rn(__ffma2_rn(__fmul2_rn(make_float2(px[i], px[i + 1]), iz), fu2, cu2), half);
       const float2 v = __fadd2_rn(__ffma2_rn(__fmul2_rn(make_float2(py[i], py[i + 1]), iz), fv2, cv2), half);
       uu[i] = u.x; uu[i + 1] = u.y;
@@ -783,7 +802,7 @@ __device__ __forceinline__ T meta_load(const T* a) {
 // Entries are handed out dynamically (blocks differ in their frame counts);
 // next[g] is double-buffered so one group barrier per entry suffices.  The
 // last CTA to finish resets every map's work list for the next batch.
-template <int NF, int NM, int G, bool COHERENT, int STORAGE, bool PINHOLE_ONLY, bool WEIGHTED>
+template <int NF, int NM, int G, bool COHERENT, int STORAGE, bool PINHOLE_ONLY, bool WEIGHTED, bool FAST>
 __device__ __forceinline__ void integrate_entries(const BatchParams<NF, NM>& p, IntegSmem<NF, NM, G>& sm) {
   static_assert(G == 1 || G == 2, "one or two worker groups per CTA");
   const int g = G == 1 ? 0 : (int)threadIdx.x / kIntegrateThreads;
@@ -856,8 +875,8 @@ __device__ __forceinline__ void integrate_entries(const BatchParams<NF, NM>& p, 
           }
         }
         fq[2] = fq[3] = -1;
-        if (nq == 2) fuse_pinhole<2, STORAGE, WEIGHTED>(p, sm.fp, fq, m, vr, D, W, G4, B, my_upd);
-        else if (nq == 1) fuse_pinhole<1, STORAGE, WEIGHTED>(p, sm.fp, fq, m, vr, D, W, G4, B, my_upd);
+        if (nq == 2) fuse_pinhole<2, STORAGE, WEIGHTED, FAST>(p, sm.fp, fq, m, vr, D, W, G4, B, my_upd);
+        else if (nq == 1) fuse_pinhole<1, STORAGE, WEIGHTED, FAST>(p, sm.fp, fq, m, vr, D, W, G4, B, my_upd);
         else if (!PINHOLE_ONLY) {
           const int f = __ffs(bits) - 1;  // a LiDAR frame
           bits &= bits - 1u;
@@ -900,12 +919,12 @@ __device__ __forceinline__ void integrate_entries(const BatchParams<NF, NM>& p, 
   }
 }
 
-template <int NF, int NM, int STORAGE, bool PINHOLE_ONLY, bool WEIGHTED>
+template <int NF, int NM, int STORAGE, bool PINHOLE_ONLY, bool WEIGHTED, bool FAST = false>
 __global__ void __launch_bounds__(kIntegrateThreads)
     integrate_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
   __shared__ IntegSmem<NF, NM, 1> sm;
   if (p.overlap) wait_prev_grid();
-  integrate_entries<NF, NM, 1, false, STORAGE, PINHOLE_ONLY, WEIGHTED>(p, sm);
+  integrate_entries<NF, NM, 1, false, STORAGE, PINHOLE_ONLY, WEIGHTED, FAST>(p, sm);
 }
 
 // ------------------------------------------- one launch per batch (fused)
@@ -969,15 +988,15 @@ union FusedSmem {
 // batches, TSDF storage, constant weighting, no walk statistics.
 // Four resident CTAs per SM (64 registers): the rig's fused step measured
 // 16.1 ms per 1,000 frames against 18.2 ms with three.
-template <int NF, int NM, int TH, int STORAGE, bool PINHOLE_ONLY>
+template <int NF, int NM, int TH, int STORAGE, bool PINHOLE_ONLY, bool FAST>
 __global__ void __launch_bounds__(kFusedThreads, 4)
     fused_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
   __shared__ FusedSmem<NF, NM, TH> sm;
   for (int cta = blockIdx.x; cta < p.alloc_ctas; cta += gridDim.x)
-    alloc_tile<NF, NM, TH, PINHOLE_ONLY, false>(p, cta, sm.a);
+    alloc_tile<NF, NM, TH, PINHOLE_ONLY, false, FAST>(p, cta, sm.a);
   if (!grid_wait(p.maps[0].ctl + 3, gridDim.x + (unsigned)p.wait_extra, p.maps[0].counters + kCntStatus))
     return;  // timed out: integration skipped, the map reports TSDF_ERR_TIMEOUT
-  integrate_entries<NF, NM, 2, true, STORAGE, PINHOLE_ONLY, false>(p, sm.i);
+  integrate_entries<NF, NM, 2, true, STORAGE, PINHOLE_ONLY, false, FAST>(p, sm.i);
 }
 
 template <int STORAGE>
@@ -1116,18 +1135,21 @@ cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile
   const dim3 g(n_ctas), b(kAllocThreads);
   if (st) {  // diagnostics: one generic variant per tile height
     if (tile_h == kTileHBig)
-      return launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, true>, g, b, s, p);
+      return launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, true, false>, g, b, s, p);
     else
-      return launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, true>, g, b, s, p);
-  } else if (tile_h == kTileHBig && ph) {
-    return launch_k(band_alloc_kernel<NF, NM, kTileHBig, true, false>, g, b, s, p);
-  } else if (tile_h == kTileHBig) {
-    return launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, false>, g, b, s, p);
-  } else if (ph) {
-    return launch_k(band_alloc_kernel<NF, NM, kTileHSmall, true, false>, g, b, s, p);
-  } else {
-    return launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, false>, g, b, s, p);
+      return launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, true, false>, g, b, s, p);
   }
+  const bool fast = p.fast_rcp != 0;
+  if (tile_h == kTileHBig) {
+    if (ph) return fast ? launch_k(band_alloc_kernel<NF, NM, kTileHBig, true, false, true>, g, b, s, p)
+                        : launch_k(band_alloc_kernel<NF, NM, kTileHBig, true, false, false>, g, b, s, p);
+    return fast ? launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, false, true>, g, b, s, p)
+                : launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, false, false>, g, b, s, p);
+  }
+  if (ph) return fast ? launch_k(band_alloc_kernel<NF, NM, kTileHSmall, true, false, true>, g, b, s, p)
+                      : launch_k(band_alloc_kernel<NF, NM, kTileHSmall, true, false, false>, g, b, s, p);
+  return fast ? launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, false, true>, g, b, s, p)
+              : launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, false, false>, g, b, s, p);
 }
 
 template <int NF, int NM>
@@ -1141,30 +1163,24 @@ cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStrea
   bool wt = false;
   for (int k = 0; k < p.n_maps; ++k) wt = wt || p.maps[k].weighting != 0;
   const dim3 g(n_ctas), b(kIntegrateThreads);
-  if (st == kStorageColor)
-    return launch_k(integrate_kernel<NF, NM, kStorageColor, true, false>, g, b, s, p);
-  else if (st == kStorageOcc && ph)
-    return launch_k(integrate_kernel<NF, NM, kStorageOcc, true, false>, g, b, s, p);
-  else if (st == kStorageOcc)
-    return launch_k(integrate_kernel<NF, NM, kStorageOcc, false, false>, g, b, s, p);
-  else if (st == kStorageX16 && wt)
-    return launch_k(integrate_kernel<NF, NM, kStorageX16, false, true>, g, b, s, p);
-  else if (st == kStorageX16 && ph)
-    return launch_k(integrate_kernel<NF, NM, kStorageX16, true, false>, g, b, s, p);
-  else if (st == kStorageX16)
-    return launch_k(integrate_kernel<NF, NM, kStorageX16, false, false>, g, b, s, p);
-  else if (st == kStorageF16 && wt)
-    return launch_k(integrate_kernel<NF, NM, kStorageF16, false, true>, g, b, s, p);
-  else if (st == kStorageF16 && ph)
-    return launch_k(integrate_kernel<NF, NM, kStorageF16, true, false>, g, b, s, p);
-  else if (st == kStorageF16)
-    return launch_k(integrate_kernel<NF, NM, kStorageF16, false, false>, g, b, s, p);
-  else if (wt)
-    return launch_k(integrate_kernel<NF, NM, kStorageF32, false, true>, g, b, s, p);
-  else if (ph)
-    return launch_k(integrate_kernel<NF, NM, kStorageF32, true, false>, g, b, s, p);
-  else
-    return launch_k(integrate_kernel<NF, NM, kStorageF32, false, false>, g, b, s, p);
+  // FAST: pinhole reciprocals by rcp_dec<true> (the host checked their range)
+  const bool fast = p.fast_rcp != 0;
+#define GBT_INTEG(ST, PH) \
+  (fast ? launch_k(integrate_kernel<NF, NM, ST, PH, false, true>, g, b, s, p) \
+        : launch_k(integrate_kernel<NF, NM, ST, PH, false, false>, g, b, s, p))
+  if (st == kStorageColor) return GBT_INTEG(kStorageColor, true);
+  if (st == kStorageOcc) return ph ? GBT_INTEG(kStorageOcc, true) : GBT_INTEG(kStorageOcc, false);
+  if (st == kStorageX16) {
+    if (wt) return launch_k(integrate_kernel<NF, NM, kStorageX16, false, true>, g, b, s, p);
+    return ph ? GBT_INTEG(kStorageX16, true) : GBT_INTEG(kStorageX16, false);
+  }
+  if (st == kStorageF16) {
+    if (wt) return launch_k(integrate_kernel<NF, NM, kStorageF16, false, true>, g, b, s, p);
+    return ph ? GBT_INTEG(kStorageF16, true) : GBT_INTEG(kStorageF16, false);
+  }
+  if (wt) return launch_k(integrate_kernel<NF, NM, kStorageF32, false, true>, g, b, s, p);
+  return ph ? GBT_INTEG(kStorageF32, true) : GBT_INTEG(kStorageF32, false);
+#undef GBT_INTEG
 }
 
 // The fused kernel of a tile height for a storage and sensor mix, launched
@@ -1172,19 +1188,24 @@ cudaError_t launch_integrate(const BatchParams<NF, NM>& p, int n_ctas, cudaStrea
 template <int NF, int NM, int TH>
 cudaError_t launch_fused_th(const BatchParams<NF, NM>& p, int st, bool ph, cudaStream_t s) {
   void (*k)(BatchParams<NF, NM>) = nullptr;
+  const bool fast = p.fast_rcp != 0;
+#define GBT_FUSED(ST) \
+  (ph ? (fast ? fused_kernel<NF, NM, TH, ST, true, true> : fused_kernel<NF, NM, TH, ST, true, false>) \
+      : (fast ? fused_kernel<NF, NM, TH, ST, false, true> : fused_kernel<NF, NM, TH, ST, false, false>))
   int si = 0;
   if (st == kStorageF32) {
-    k = ph ? fused_kernel<NF, NM, TH, kStorageF32, true> : fused_kernel<NF, NM, TH, kStorageF32, false>;
+    k = GBT_FUSED(kStorageF32);
     si = 0;
   } else if (st == kStorageF16) {
-    k = ph ? fused_kernel<NF, NM, TH, kStorageF16, true> : fused_kernel<NF, NM, TH, kStorageF16, false>;
+    k = GBT_FUSED(kStorageF16);
     si = 1;
   } else {
-    k = ph ? fused_kernel<NF, NM, TH, kStorageX16, true> : fused_kernel<NF, NM, TH, kStorageX16, false>;
+    k = GBT_FUSED(kStorageX16);
     si = 2;
   }
-  static int per_sm[3][2] = {};  // resident CTAs per SM of each variant (all devices are alike here)
-  int& n = per_sm[si][ph ? 1 : 0];
+#undef GBT_FUSED
+  static int per_sm[3][2][2] = {};  // resident CTAs per SM of each variant (all devices are alike here)
+  int& n = per_sm[si][ph ? 1 : 0][fast ? 1 : 0];
   if (n == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kFusedThreads, 0) != cudaSuccess) {
     n = 0;
     return cudaGetLastError();

@@ -6,6 +6,7 @@
 // per-voxel integrator (Sec. IV-B).  Nothing here touches voxel data.
 #include <algorithm>
 #include <array>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -24,6 +25,7 @@ struct LidarTable {
   int32_t n_az, n_el;
   float theta_start, phi_start, el_fov;
   float* dev;  // float2 [n_az] (cos, sin azimuth) then float2 [n_el] (cos, sin polar)
+  int lsb;     // smallest last-place exponent of a nonzero beam direction component (fast_rcp_ok)
 };
 
 struct tsdf_map {
@@ -142,13 +144,81 @@ bool valid_lidar(const tsdf_lidar* c) {
          std::isfinite(c->max_range) && c->min_range <= c->max_range;
 }
 
+// Exponent of the last place of a nonzero FP32 value (subnormals: -149).
+int lsb_exp(float x) {
+  int e = 0;
+  std::frexp(x, &e);  // |x| = f 2^e, f in [0.5, 1)
+  return std::max(e - 24, -149);
+}
+
+constexpr double kTwo126 = 8.507059173023462e37;  // 2^126
+
+// Range check for the kernels' fast reciprocal (rcp_dec<true>, exact for
+// |x| in [2^-126, 2^126]).  Every value a frame's decisions invert is an
+// FMA chain of FP32 terms, sum_k a_k b_k + c: a traversal direction
+// component d = M_k0 r_x + (M_k1 r_y + M_k2) (pinhole, r the pixel's ray)
+// or M_k0 b_x + (M_k1 b_y + RN(M_k2 b_z)) (LiDAR, b the beam direction), and
+// a voxel depth z = R_20 q_x + (R_21 q_y + (R_22 q_z + t_2)) (pinhole
+// projection; q the voxel centre, |q| >= v / 2).  The exact sum is a
+// multiple of 2^L, L the smallest last-place exponent among the products
+// (lsb a + lsb b) and the addend, and each rounding in the chain keeps it
+// so, hence a nonzero result has magnitude >= 2^L.  With L >= -126 and the
+// magnitudes bounded below 2^126 every nonzero value is in range; zeros are
+// never inverted (a zero direction component has no crossing, z <= 0 fails
+// the projection test).  lidar_lsb: the table's smallest beam-component
+// last-place exponent.
+bool fast_rcp_ok(const FrameDev& F, double v, int lidar_lsb) {
+  int lsb_m = INT_MAX;
+  double max_m = 0.0;
+  for (int i = 0; i < 9; ++i)
+    if (F.M[i] != 0.0f) {
+      lsb_m = std::min(lsb_m, lsb_exp(F.M[i]));
+      max_m = std::max(max_m, (double)std::fabs(F.M[i]));
+    }
+  if (lsb_m == INT_MAX) return false;
+  if (F.kind == TSDF_SENSOR_PINHOLE) {
+    int lsb_r = INT_MAX;
+    double max_r = 1.0;
+    for (int i = 0; i < F.width; ++i) {
+      const float r = ((float)i - F.cu) / F.fu;  // as the allocation kernel forms it
+      if (r != 0.0f) lsb_r = std::min(lsb_r, lsb_exp(r));
+      max_r = std::max(max_r, (double)std::fabs(r));
+    }
+    for (int j = 0; j < F.height; ++j) {
+      const float r = ((float)j - F.cv) / F.fv;
+      if (r != 0.0f) lsb_r = std::min(lsb_r, lsb_exp(r));
+      max_r = std::max(max_r, (double)std::fabs(r));
+    }
+    const int L = std::min(lsb_m, lsb_r == INT_MAX ? lsb_m : lsb_m + lsb_r);
+    if (L < -126 || 3.0 * max_m * max_r * (1.0 + 1e-6) >= kTwo126) return false;
+    // projection: z of a voxel centre
+    int lsb_rc = INT_MAX;
+    double max_rc = 0.0;
+    for (int j = 6; j < 9; ++j)
+      if (F.Rcl[j] != 0.0f) {
+        lsb_rc = std::min(lsb_rc, lsb_exp(F.Rcl[j]));
+        max_rc = std::max(max_rc, (double)std::fabs(F.Rcl[j]));
+      }
+    const float half_v = 0.5f * (float)v;  // the smallest |q| (q = (rel + 1/2) v, rel an integer)
+    if (!(half_v >= 1.17549435e-38f)) return false;
+    int L2 = lsb_rc == INT_MAX ? INT_MAX : lsb_rc + lsb_exp(half_v);
+    if (F.tloc[2] != 0.0f) L2 = std::min(L2, lsb_exp(F.tloc[2]));
+    const double max_q = (16777216.0 + 16.0) * (double)(float)v * (1.0 + 1e-6);  // |rel| < 2^24 + 8
+    if (L2 < -126 || 3.0 * max_rc * max_q + std::fabs((double)F.tloc[2]) >= kTwo126) return false;
+    return true;
+  }
+  const int L = lidar_lsb == INT_MAX ? lsb_m : lsb_m + lidar_lsb;  // beam components are at most 1
+  return L >= -126 && 3.0 * max_m * (1.0 + 1e-6) < kTwo126;
+}
+
 // Beam-centre direction tables of a LiDAR (Eq. 3 inverted at the cell
 // centres), computed in FP64 and rounded once; uploaded on first use.
-tsdf_status lidar_table(tsdf_map* m, const tsdf_lidar* c, const float** out) {
+tsdf_status lidar_table(tsdf_map* m, const tsdf_lidar* c, const float** out, int* lsb) {
   for (const LidarTable& t : m->tables)
     if (t.n_az == c->n_az && t.n_el == c->n_el && t.theta_start == c->theta_start &&
         t.phi_start == c->phi_start && t.el_fov == c->el_fov) {
       *out = t.dev;
+      *lsb = t.lsb;
       return TSDF_OK;
     }
   std::vector<float> h(2 * ((size_t)c->n_az + c->n_el));
@@ -162,7 +232,21 @@ tsdf_status lidar_table(tsdf_map* m, const tsdf_lidar* c, const float** out) {
     h[2 * (c->n_az + j)] = (float)std::cos(ph);
     h[2 * (c->n_az + j) + 1] = (float)std::sin(ph);
   }
-  LidarTable t{c->n_az, c->n_el, c->theta_start, c->phi_start, c->el_fov, nullptr};
+  // beam direction components the traversal uses: sin(polar) cos / sin(azimuth)
+  // (FP32 products, as the kernel forms them) and cos(polar)
+  int low = INT_MAX;
+  auto note = [&low](float x) {
+    if (x != 0.0f) low = std::min(low, lsb_exp(x));
+  };
+  for (int j = 0; j < c->n_el; ++j) {
+    const float sp = h[2 * (c->n_az + j) + 1];
+    note(h[2 * (c->n_az + j)]);
+    for (int k = 0; k < c->n_az; ++k) {
+      note(sp * h[2 * k]);
+      note(sp * h[2 * k + 1]);
+    }
+  }
+  LidarTable t{c->n_az, c->n_el, c->theta_start, c->phi_start, c->el_fov, nullptr, low};
   if (cudaMalloc(&t.dev, h.size() * sizeof(float)) != cudaSuccess) return cuda_fail();
   if (cudaMemcpy(t.dev, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(t.dev);
@@ -170,6 +254,7 @@ tsdf_status lidar_table(tsdf_map* m, const tsdf_lidar* c, const float** out) {
   }
   m->tables.push_back(t);
   *out = t.dev;
+  *lsb = t.lsb;
   return TSDF_OK;
 }
 
@@ -179,6 +264,7 @@ tsdf_status fill_frame(tsdf_map* m, int map_index, int kind, const tsdf_pinhole*
                        const tsdf_lidar* li, const float* depth, const uint32_t* rgba,
                        const double* T, FrameDev& F) {
   std::memset(&F, 0, sizeof(F));
+  int lidar_lsb = INT_MAX;
   if (!depth || !T || !rigid(T)) return TSDF_ERR_ARG;
   const bool color = m->storage == gbt::kStorageColor;
   if (color != (rgba != nullptr) || (color && kind != TSDF_SENSOR_PINHOLE)) return TSDF_ERR_ARG;
@@ -204,12 +290,13 @@ tsdf_status fill_frame(tsdf_map* m, int map_index, int kind, const tsdf_pinhole*
     F.beta = (float)((double)li->n_el / (double)li->el_fov);
     F.min_range = li->min_range;
     F.max_range = li->max_range;
-    tsdf_status st = lidar_table(m, li, &F.tab);
+    tsdf_status st = lidar_table(m, li, &F.tab, &lidar_lsb);
     if (st != TSDF_OK) return st;
   } else {
     return TSDF_ERR_ARG;
   }
   if (!prepare_pose(m->Bd, T, F)) return TSDF_ERR_ARG;
+  F.fast_rcp = fast_rcp_ok(F, m->vd, lidar_lsb) ? 1 : 0;
   return TSDF_OK;
 }
 
@@ -261,6 +348,7 @@ tsdf_status integrate_one(tsdf_map* m, int kind, const tsdf_pinhole* ph, const t
   if (st != TSDF_OK) return st;
   p.fr[0].blk_begin = 0;
   p.fr[0].bit = 0;
+  p.fast_rcp = p.fr[0].fast_rcp;
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t* ev = timing_slot(m);
   if (ev) cudaEventRecord(ev[0], s);
@@ -557,6 +645,8 @@ tsdf_status run_batch(tsdf_map* const* maps, int32_t n_maps, std::vector<FrameDe
       }
       p1.alloc_ctas = ctas;
       p1.wait_extra = lead->wait_extra;
+      p1.fast_rcp = 1;
+      for (int f = 0; f < nf; ++f) p1.fast_rcp &= p1.fr[f].fast_rcp;
       cudaEvent_t* ev = timing_slot(lead);
       if (ev) cudaEventRecord(ev[0], s);
       cudaError_t err = gbt::launch_fused(p1, th, s);
@@ -602,9 +692,11 @@ tsdf_status run_batch(tsdf_map* const* maps, int32_t n_maps, std::vector<FrameDe
     p.n_maps = n_maps;
     for (int i = 0; i < n_maps; ++i) p.maps[i] = view_set(maps[i], piped ? (b & 1) : 0);
     int64_t pixels = 0;
+    p.fast_rcp = 1;
     for (int f = 0; f < nf; ++f) {
       p.fr[f] = fr[f0 + f];
       p.fr[f].bit = f;
+      p.fast_rcp &= p.fr[f].fast_rcp;
       pixels += (int64_t)p.fr[f].width * p.fr[f].height;
     }
     const int th = lead->tile_h ? lead->tile_h : pick_tile_h(pixels);
@@ -618,6 +710,7 @@ tsdf_status run_batch(tsdf_map* const* maps, int32_t n_maps, std::vector<FrameDe
     if (n_maps == 1) {
       p1.n_frames = p.n_frames;
       p1.n_maps = 1;
+      p1.fast_rcp = p.fast_rcp;
       p1.maps[0] = p.maps[0];
       std::memcpy(p1.fr, p.fr, sizeof(p.fr));
     }
@@ -1384,6 +1477,7 @@ tsdf_status integrate_depth_static(const tsdf_map_buffers* buf, float voxel_size
   F.blk_begin = 0;
   F.bit = 0;
   if (!prepare_pose(8.0 * (double)voxel_size, T_world_cam, F)) return TSDF_ERR_ARG;
+  p.fast_rcp = fast_rcp_ok(F, (double)voxel_size, INT_MAX) ? 1 : 0;
 
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||

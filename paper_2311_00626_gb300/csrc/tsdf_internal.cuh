@@ -148,6 +148,7 @@ struct FrameDev {
   int32_t a[3];
   int32_t blk_begin;     // first allocation CTA of this frame
   int32_t bit;           // bit of this frame in the slot masks = its index in the batch
+  int32_t fast_rcp;      // host check: this frame's inverted decision values are in [2^-126, 2^126]
 };
 
 template <int NF, int NM>
@@ -157,6 +158,7 @@ struct BatchParams {
   int32_t overlap;     // launched as a programmatic dependent of the stream's previous kernel
   int32_t alloc_ctas;  // allocation tiles of the batch (the fused kernel loops over them)
   int32_t wait_extra;  // test hook: the fused kernel's grid wait expects this many extra CTAs
+  int32_t fast_rcp;    // every reciprocal of the batch's decisions lies in [2^-126, 2^126] or is not taken
   MapDev maps[NM];
   FrameDev fr[NF];
 };

@@ -91,6 +91,35 @@ def test_tilted_plane_far_pose(seed, origin):
     _parity(f"tilted{seed}", [Frame(cam, T, d)], 0.05, tol_pinhole(0.05))
 
 
+def test_tiny_rotation_entries_ieee_reciprocals():
+    """A camera rotated by 1e-37 rad about x: the ray-direction terms fall
+    below the range where the kernels' fast reciprocal is exact (2^-126), so
+    the host selects the IEEE-reciprocal kernels for the frame; the result
+    still equals the oracle's.  A second frame of ordinary pose in the same
+    batch makes the whole batch take the IEEE kernels."""
+    eps = 1e-37
+    T = np.eye(4)
+    T[1, 1] = T[2, 2] = np.cos(eps)
+    T[1, 2], T[2, 1] = -np.sin(eps), np.sin(eps)
+    T[:3, 3] = (0.31, -0.17, 0.05)
+    cam = synth.pinhole(48, 36, 40.0)
+    prims = synth.scene(synth.prim(synth.PLANE, 0.0, 0.0, 1.0, 2.1),
+                        synth.prim(synth.SPHERE, 0.2, 0.1, 1.6, 0.3))
+    frames = []
+    for Tk in (T, _plain_pose()):
+        d = synth.render_pinhole(prims, Tk, cam["fu"], cam["fv"], cam["cu"], cam["cv"], 48, 36,
+                                 max_depth=6.0)
+        frames.append(Frame(cam, Tk, d))
+    _parity("tiny_rotation", frames[:1], 0.05, tol_pinhole(0.05))
+    _parity("tiny_rotation_batch", frames, 0.05, tol_pinhole(0.05), batch=2)
+
+
+def _plain_pose():
+    T = np.eye(4)
+    T[:3, 3] = (0.05, 0.02, -0.1)
+    return T
+
+
 def test_room_frames_640x480():
     """Twelve full-size frames of the room sequence (several thousand blocks,
     many CTAs and warps per frame, ragged last CTA of pixels)."""
