@@ -588,7 +588,7 @@ struct __align__(16) FrameProj {
   float4 r0, r1, r2;  // rows of R_CL, with t_loc in w
   float4 cam;         // fu, fv, cu, cv
   int4 anchor;        // a, width
-  float4 size;        // width, height (as floats), unused, unused
+  float4 size;        // width, height (as floats), height (integer bits), unused
 };
 
 __device__ __forceinline__ void stage_frame(const FrameDev& F, FrameProj& S) {
@@ -597,7 +597,7 @@ __device__ __forceinline__ void stage_frame(const FrameDev& F, FrameProj& S) {
   S.r2 = make_float4(F.Rcl[6], F.Rcl[7], F.Rcl[8], F.tloc[2]);
   S.cam = make_float4(F.fu, F.fv, F.cu, F.cv);
   S.anchor = make_int4(F.a[0], F.a[1], F.a[2], F.width);
-  S.size = make_float4((float)F.width, (float)F.height, 0.0f, 0.0f);
+  S.size = make_float4((float)F.width, (float)F.height, __int_as_float(F.height), 0.0f);
 }
 
 // row_points with staged constants (same arithmetic).
@@ -665,13 +665,24 @@ __device__ __forceinline__ void fuse_pinhole(const P& p, const FrameProj* s_fp, 
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const float u = uu[i], v = vv[i];
-      const bool in = z[q][i] > 0.0f && u >= 0.0f && u < size.x && v >= 0.0f && v < size.y;
+      bool in;
+      int pix;
+      if (FAST) {
+        // pixel = floor(u), valid iff 0 <= u < W: one unsigned comparison of
+        // the floored value per axis (u is finite here: z > 0 implies
+        // z >= 2^-126 in FAST batches, so 1 / z is finite)
+        const int iu = __float2int_rd(u), iv = __float2int_rd(v);
+        in = z[q][i] > 0.0f && (unsigned)iu < (unsigned)an.w && (unsigned)iv < (unsigned)__float_as_int(size.z);
+        pix = iv * an.w + iu;
+      } else {
+        in = z[q][i] > 0.0f && u >= 0.0f && u < size.x && v >= 0.0f && v < size.y;
+        pix = (int)v * an.w + (int)u;
+      }
       if (STORAGE == kStorageColor) {
-        const int pix = in ? (int)v * an.w + (int)u : 0;
         d[q][i] = in ? __ldg(depth + pix) : 0.0f;
         c[q][i] = in ? __ldg(p.fr[fq[q]].rgba + pix) : 0u;
       } else {
-        d[q][i] = in ? __ldg(depth + (int)v * an.w + (int)u) : 0.0f;
+        d[q][i] = in ? __ldg(depth + pix) : 0.0f;
       }
     }
   }
