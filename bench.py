@@ -240,6 +240,9 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="simulated seconds of Poisson arrivals (the paced run takes as long)")
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct poses per map")
+    ap.add_argument("--serve-max-blocks", type=int, default=0,
+                    help="pool blocks per serving map (0: the library default); smaller maps keep a "
+                         "profiler capture of the serving workload within a few GB of device memory")
     ap.add_argument("--no-rig", action="store_true", help="leave the rig form out of the default line")
     ap.add_argument("--no-serving", action="store_true",
                     help="leave the serving form out of the default line")
@@ -922,7 +925,8 @@ def serving_form(args, torch, storage: int = 1) -> dict:
     cfg, reqs, distinct = _serving_requests(torch, args.serve_seconds, args.serve_pool)
     # the maps persist across runs (reset in between): per-map set-up
     # (sensor tables, the copy stream) stays outside the timed runs
-    maps = [gt.TsdfMap(c["voxel_size"], c["truncation_voxels"], c["max_weight"], storage=storage)
+    maps = [gt.TsdfMap(c["voxel_size"], c["truncation_voxels"], c["max_weight"], storage=storage,
+                       max_blocks=args.serve_max_blocks)
             for c in cfg]
     in_bytes = sum(r.nbytes for r in reqs)
 
