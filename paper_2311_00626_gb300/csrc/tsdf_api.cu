@@ -177,18 +177,27 @@ bool fast_rcp_ok(const FrameDev& F, double v, int lidar_lsb) {
     }
   if (lsb_m == INT_MAX) return false;
   if (F.kind == TSDF_SENSOR_PINHOLE) {
+    // pixel ray components r = (i - c) / f, as the allocation kernel forms
+    // them: monotone in i (every rounding is), so the largest |r| is at an
+    // image edge and the smallest nonzero |r| next to the principal point;
+    // those few pixels bound the whole image
     int lsb_r = INT_MAX;
     double max_r = 1.0;
-    for (int i = 0; i < F.width; ++i) {
-      const float r = ((float)i - F.cu) / F.fu;  // as the allocation kernel forms it
-      if (r != 0.0f) lsb_r = std::min(lsb_r, lsb_exp(r));
-      max_r = std::max(max_r, (double)std::fabs(r));
-    }
-    for (int j = 0; j < F.height; ++j) {
-      const float r = ((float)j - F.cv) / F.fv;
-      if (r != 0.0f) lsb_r = std::min(lsb_r, lsb_exp(r));
-      max_r = std::max(max_r, (double)std::fabs(r));
-    }
+    auto bound = [&](int n, float c, float f) {
+      const double cl = std::floor((double)c);
+      const int cand[6] = {0, n - 1, (int)std::max(-1.0, std::min((double)n, cl - 1.0)),
+                           (int)std::max(-1.0, std::min((double)n, cl)),
+                           (int)std::max(-1.0, std::min((double)n, cl + 1.0)),
+                           (int)std::max(-1.0, std::min((double)n, cl + 2.0))};
+      for (int i : cand) {
+        if (i < 0 || i >= n) continue;
+        const float r = ((float)i - c) / f;
+        if (r != 0.0f) lsb_r = std::min(lsb_r, lsb_exp(r));
+        max_r = std::max(max_r, (double)std::fabs(r));
+      }
+    };
+    bound(F.width, F.cu, F.fu);
+    bound(F.height, F.cv, F.fv);
     const int L = std::min(lsb_m, lsb_r == INT_MAX ? lsb_m : lsb_m + lsb_r);
     if (L < -126 || 3.0 * max_m * max_r * (1.0 + 1e-6) >= kTwo126) return false;
     // projection: z of a voxel centre
