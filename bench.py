@@ -243,6 +243,9 @@ def main():
     ap.add_argument("--serve-max-blocks", type=int, default=0,
                     help="pool blocks per serving map (0: the library default); smaller maps keep a "
                          "profiler capture of the serving workload within a few GB of device memory")
+    ap.add_argument("--launch-shape", default="",
+                    help="room launch shape as TILE_H,CTAS_PER_SM (e.g. 32,0) instead of the autotuner's pick; "
+                         "for profiling commands, whose launch counts must not depend on the tuning")
     ap.add_argument("--no-rig", action="store_true", help="leave the rig form out of the default line")
     ap.add_argument("--no-serving", action="store_true",
                     help="leave the serving form out of the default line")
@@ -321,8 +324,12 @@ def main():
         mt.close()
         return a.elapsed_time(b) / 3
 
-    shapes = [{"alloc_tile_h": t, "integrate_ctas_per_sm": c} for t in (16, 32) for c in (0, 3, 4, 5)]
-    shape, shape_timings = autotune(f"room{args.batch}", time_shape, shapes, cache=False)
+    if args.launch_shape:
+        th, cp = (int(x) for x in args.launch_shape.split(","))
+        shape, shape_timings = {"alloc_tile_h": th, "integrate_ctas_per_sm": cp}, []
+    else:
+        shapes = [{"alloc_tile_h": t, "integrate_ctas_per_sm": c} for t in (16, 32) for c in (0, 3, 4, 5)]
+        shape, shape_timings = autotune(f"room{args.batch}", time_shape, shapes, cache=False)
 
     # ---- headline: FP32 storage, batched launches
     m = gt.TsdfMap(w.voxel_size, w.truncation_voxels, w.max_weight, storage=gt.STORAGE_FP32, **shape)
