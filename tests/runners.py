@@ -34,16 +34,22 @@ def to_device(frames):
 
 
 def run_gpu(frames, voxel_size, trunc=4, wmax=100.0, storage=0, batch=1, lidar_nearest=False,
-            guard=0.0, max_blocks=0, keep=False, occupancy=None, weighting=0):
+            guard=0.0, max_blocks=0, keep=False, occupancy=None, weighting=0, walk_stats=True):
     """Integrate `frames` (in order) into a fresh map, `batch` frames per
-    integrate_batch call (batch=1: integrate_depth / integrate_lidar)."""
+    integrate_batch call (batch=1: integrate_depth / integrate_lidar).
+
+    walk_stats: count walked cells (stats["cells"]), which selects the
+    allocator variant with the counters; False runs the variants the
+    benchmark times (pinhole-only batches, refined reciprocals where the
+    host's range check allows) and leaves the cell count at 0."""
     import torch
     import paper_2311_00626_gb300 as gt
     occ = {} if occupancy is None else {"layer": gt.LAYER_OCCUPANCY, "l_occ": occupancy[0],
                                         "l_free": occupancy[1]}
     m = gt.TsdfMap(voxel_size, trunc, wmax, storage=storage, max_blocks=max_blocks,
                    lidar_nearest=lidar_nearest, lidar_guard=guard, weighting=weighting, **occ)
-    gt.map_walk_stats(m.handle, True)  # the tests compare walked cells with the oracle's
+    if walk_stats:
+        gt.map_walk_stats(m.handle, True)  # the tests compare walked cells with the oracle's
     dev = to_device(frames)
     if batch == 1:
         for f, d in zip(frames, dev):

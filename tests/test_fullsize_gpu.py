@@ -55,6 +55,19 @@ def test_room_300_frames_fp32(room):
     _record("room300_fp32", {**st, "max_err_vox": st["max_err"] / v, "rms_err_vox": st["rms_err"] / v})
 
 
+def test_room_300_frames_fp32_benchmark_kernels(room):
+    """The kernel variants the benchmark times (no walk counters: the
+    pinhole-only allocator with refined reciprocals) against the oracle."""
+    w, orc, oc = room
+    gpu, gs, status = run_gpu(w.frames, w.voxel_size, batch=BATCH, walk_stats=False)
+    assert status == 0
+    st = compare(gpu, orc, 1e-4 * float(np.float32(w.voxel_size)), "room300_fp32_bench_kernels")
+    assert gs["voxel_updates"] == oc["total_updates"]
+    assert gs["block_frame_pairs"] == oc["total_band_blocks"]
+    assert gs["cells"] == 0  # the counting variant did not run
+    _record("room300_fp32_bench_kernels", st)
+
+
 def test_room_300_frames_one_call_pipelined(room):
     """All 300 frames in one integrate_batch call (ten pipelined sub-batches)."""
     w, orc, oc = room

@@ -257,6 +257,62 @@ def test_dda_matches_slab_test():
     assert n_checked == 3000
 
 
+def _exact_walk(o, d, s0, s1):
+    """Cells of o + s d, s in [s0, s1] (block units), in the order the
+    segment enters them, in FP64.  None where FP32 rounding may decide
+    otherwise: the start point within 1e-4 of a cell face, or two crossings
+    (or a crossing and an end of the segment) closer than 1e-5 relative."""
+    p = o + s0 * d
+    if np.any(np.abs(p - np.round(p)) < 1e-4):
+        return None
+    c = np.floor(p).astype(np.int64)
+    events = []
+    for k in range(3):
+        if d[k] == 0.0:
+            continue
+        step = 1 if d[k] > 0 else -1
+        b = c[k] + (1 if step > 0 else 0)
+        while True:
+            t = (b - o[k]) / d[k]
+            if t > s1 * (1 + 1e-5) + 1e-5:
+                break
+            events.append((t, k, step))
+            b += step
+    events.sort()
+    ts = [s0] + [e[0] for e in events] + [s1]
+    if any(b - a < 1e-5 * max(1.0, abs(b)) for a, b in zip(ts, ts[1:])):
+        return None
+    cells = [tuple(c)]
+    for _, k, step in events:
+        c[k] += step
+        cells.append(tuple(c))
+    return cells
+
+
+def test_dda_cap_keeps_the_first_cells():
+    """Segments of 20-80 blocks: the traversal stops after kMaxCells = 32
+    cells, and those are the first 32 cells the segment enters (checked
+    against an FP64 walk that orders every crossing exactly)."""
+    rng = np.random.default_rng(12)
+    checked = capped = 0
+    for _ in range(1500):
+        o = rng.uniform(0, 1, 3).astype(np.float32)
+        d = (rng.normal(size=3) * rng.uniform(0.5, 3)).astype(np.float32)
+        if rng.uniform() < 0.2:
+            d[rng.integers(3)] = 0.0
+        nd = float(np.linalg.norm(d.astype(np.float64)))
+        s0 = np.float32(rng.uniform(0, 4))
+        s1 = np.float32(s0 + rng.uniform(20, 80) / nd)
+        exp = _exact_walk(o.astype(np.float64), d.astype(np.float64), float(s0), float(s1))
+        if exp is None:
+            continue
+        got = [tuple(c) for c in oracle.dda(o, d, float(s0), float(s1)).tolist()]
+        assert got == exp[:32], (o, d, s0, s1)
+        checked += 1
+        capped += len(exp) > 32
+    assert checked >= 1000 and capped >= 900, (checked, capped)
+
+
 # ------------------------------------------------------------------ LiDAR
 
 

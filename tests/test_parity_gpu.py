@@ -52,7 +52,7 @@ def _rot(rng):
 
 
 def _parity(name, frames, v, tol, **kw):
-    orc, oc = run_oracle(frames, v, lidar_nearest=kw.get("lidar_nearest", False),
+    orc, oc = run_oracle(frames, v, trunc=kw.get("trunc", 4), lidar_nearest=kw.get("lidar_nearest", False),
                          guard=kw.get("guard", 0.0))
     gpu, gs, status = run_gpu(frames, v, **kw)
     assert status == 0, f"device status {status}"
@@ -60,9 +60,11 @@ def _parity(name, frames, v, tol, **kw):
     assert gs["voxel_updates"] == oc["total_updates"], (gs, oc)
     # the allocator emitted exactly the oracle's cells (same walks), and every
     # frame's band set reached the integration (one (block, frame) pair each)
-    assert gs["cells"] == oc["total_cells"], (gs, oc)
+    if kw.get("walk_stats", True):
+        assert gs["cells"] == oc["total_cells"], (gs, oc)
     assert gs["block_frame_pairs"] == oc["total_band_blocks"], (gs, oc)
     _record(name, st)
+    st["oracle_counters"] = oc
     return st
 
 
@@ -72,6 +74,29 @@ def test_tiny_plane_sphere():
     w = synth.config_tiny()
     st = _parity("tiny", w.frames, w.voxel_size, tol_pinhole(w.voxel_size))
     assert st["blocks"] > 50
+
+
+@pytest.mark.parametrize("batch", [1, 8])
+def test_benchmark_kernel_variants(batch):
+    """Without walk counters the allocator runs the variants the benchmark
+    times (pinhole-only, refined reciprocals): the tiny scene and room
+    frames against the oracle, one frame per call and batched."""
+    w = synth.config_tiny()
+    _parity(f"tiny_bench_kernels_b{batch}", w.frames, w.voxel_size, tol_pinhole(w.voxel_size),
+            batch=batch, walk_stats=False)
+    r = synth.config_room(n_frames=300)
+    _parity(f"room16_bench_kernels_b{batch}", r.frames[40:56], r.voxel_size, tol_pinhole(r.voxel_size),
+            batch=batch, walk_stats=False)
+
+
+@pytest.mark.parametrize("walk_stats", [True, False])
+def test_walk_cap_long_band(walk_stats):
+    """A 160-voxel truncation at 1 cm (band 3.2 m, 40 blocks deep): walks
+    stop after kMaxCells = 32 cells on both sides, the same cells."""
+    w = synth.config_tiny()
+    st = _parity(f"walk_cap_ws{int(walk_stats)}", w.frames, 0.01, tol_pinhole(0.01), trunc=160,
+                 walk_stats=walk_stats)
+    assert st["oracle_counters"]["truncated_rays"] > 1000
 
 
 @pytest.mark.parametrize("seed,origin", [(1, (103.7, -52.1, 7.3)), (3, (-2001.13, 17.9, -3.31))])
