@@ -182,8 +182,10 @@ constexpr uint32_t kFarFlag = 1u << 30;  // key counted from the segment's own s
 
 // CTA-local set of relative block keys (open addressing in shared memory).
 // Returns false when the key could not be placed within kSetProbes slots;
-// the caller then claims it globally itself.
-__device__ __noinline__ bool set_insert_slow(uint32_t* set, uint32_t key, uint32_t h);
+// the caller then claims it globally itself.  The probing loop is inlined:
+// at the allocator's 32 registers a call's saves and restores cost more
+// than the larger code (measured 5 % slower as a call).
+__device__ __forceinline__ bool set_insert_slow(uint32_t* set, uint32_t key, uint32_t h);
 
 __device__ __forceinline__ bool set_insert(uint32_t* set, uint32_t key) {
   const uint32_t h = (key * 0x9E3779B1u) >> (32 - kSetBits);
@@ -192,7 +194,7 @@ __device__ __forceinline__ bool set_insert(uint32_t* set, uint32_t key) {
   return set_insert_slow(set, key, h);
 }
 
-__device__ __noinline__ bool set_insert_slow(uint32_t* set, uint32_t key, uint32_t h) {
+__device__ __forceinline__ bool set_insert_slow(uint32_t* set, uint32_t key, uint32_t h) {
   volatile uint32_t* vs = set;
 #pragma unroll 1
   for (int probe = 0; probe < kSetProbes; ++probe) {
