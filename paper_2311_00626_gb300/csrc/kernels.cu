@@ -105,8 +105,8 @@ __device__ __forceinline__ void claim_block(const MapDev& m, unsigned long long 
 // Walk in anchor-relative cell coordinates with a 32-bit key
 // (cx + 512) | (cy + 512) << 10 | (cz + 512) << 20; used when the segment
 // starts within kRelStart cells of the anchor, so that every cell of the walk
-// (at most kMaxCells steps) stays inside the 10-bit fields.  Same decision
-// sequence as Walk.
+// (at most kMaxCells steps) stays inside the 10-bit fields.  The decisions
+// are the prescribed FP32 sequence of the traversal, cell for cell.
 constexpr int kRelBias = 512;
 constexpr float kRelStart = 470.0f;
 constexpr uint32_t kEmptyRel = 0xFFFFFFFFu;
@@ -119,36 +119,39 @@ struct Walk32 {
   uint32_t key;
   uint32_t kx, ky, kz;  // key change of one step along each axis (+unit, -unit, 0)
   float bx, by, bz;     // next boundary per axis (+inf for an axis the ray does not cross)
-  float ix, iy, iz;
-  float tx, ty, tz;
+  float ix, iy, iz;      // reciprocal direction per axis
   float s1;
   int n;
 
   // t of an axis is always (b - o) * inv; an axis with zero direction has
   // b = +inf and inv = 1, so its t is +inf.
   template <bool FAST>
-  __device__ __forceinline__ void axis(float d, float fl, float o, uint32_t unit, uint32_t& k,
-                                       float& inv, float& b, float& t) {
+  __device__ __forceinline__ void axis(float d, float fl, uint32_t unit, uint32_t& k, float& inv, float& b) {
     const bool pos = d > 0.0f, neg = d < 0.0f;
     k = pos ? unit : (neg ? 0u - unit : 0u);
     inv = (pos || neg) ? rcp_dec<FAST>(d) : 1.0f;
     b = pos ? fl + 1.0f : (neg ? fl : __int_as_float(0x7f800000));
-    t = __fmul_rn(__fsub_rn(b, o), inv);
   }
   template <bool FAST>
-  __device__ __forceinline__ void start(float px, float py, float pz, float ox_, float oy_, float oz_,
-                                        float dx, float dy, float dz, float s1_, int bx0, int by0,
-                                        int bz0, uint32_t flag) {
+  __device__ __forceinline__ void start(float px, float py, float pz, float dx, float dy, float dz,
+                                        float s1_, int bx0, int by0, int bz0, uint32_t flag) {
     const float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
     key = ((uint32_t)((int)flx - bx0 + kRelBias) | ((uint32_t)((int)fly - by0 + kRelBias) << 10) |
            ((uint32_t)((int)flz - bz0 + kRelBias) << 20)) | flag;
-    axis<FAST>(dx, flx, ox_, 1u, kx, ix, bx, tx);
-    axis<FAST>(dy, fly, oy_, 1u << 10, ky, iy, by, ty);
-    axis<FAST>(dz, flz, oz_, 1u << 20, kz, iz, bz, tz);
+    axis<FAST>(dx, flx, 1u, kx, ix, bx);
+    axis<FAST>(dy, fly, 1u << 10, ky, iy, by);
+    axis<FAST>(dz, flz, 1u << 20, kz, iz, bz);
     s1 = s1_;
     n = 1;
   }
+  // The crossing parameters are recomputed from the boundaries at every
+  // step, not carried: they are dead while the cell's key is recorded (at 32
+  // registers a thread, carrying them spilled 88 bytes; 94.6 against 97.7 us
+  // per 32-frame launch).
   __device__ __forceinline__ bool next(float ox, float oy, float oz) {
+    const float tx = __fmul_rn(__fsub_rn(bx, ox), ix);
+    const float ty = __fmul_rn(__fsub_rn(by, oy), iy);
+    const float tz = __fmul_rn(__fsub_rn(bz, oz), iz);
     const bool sy_ = ty < tx;
     const float t01 = fminf(tx, ty);
     const bool sz_ = tz < t01;
@@ -160,13 +163,10 @@ struct Walk32 {
     // the boundary moves by +1 or -1 along the stepped axis: the sign of its
     // key change (never 0: an axis the ray does not cross has t = +inf)
     const float f = __uint_as_float((dk & 0x80000000u) | 0x3f800000u);
-    bx += sx_ ? f : 0.0f;
-    by += syy ? f : 0.0f;
-    bz += sz_ ? f : 0.0f;
-    // recomputing the unchanged axes reproduces their t exactly
-    tx = __fmul_rn(__fsub_rn(bx, ox), ix);
-    ty = __fmul_rn(__fsub_rn(by, oy), iy);
-    tz = __fmul_rn(__fsub_rn(bz, oz), iz);
+    // predicated additions (an unconditional add of 0 costs a select more)
+    if (sx_) bx = __fadd_rn(bx, f);
+    if (syy) by = __fadd_rn(by, f);
+    if (sz_) bz = __fadd_rn(bz, f);
     ++n;
     return true;
   }
@@ -212,21 +212,25 @@ __device__ __forceinline__ bool set_insert_slow(uint32_t* set, uint32_t key, uin
 // Band segment of pixel (i, j) (Sec. IV-B ray through the block grid): ray
 // direction in anchor-relative block units per unit of depth (camera) or
 // range (LiDAR) and the band [max(d - tau, 0), d + tau].  False if the pixel
-// is outside the image or its depth is invalid.
+// is outside the image or its depth is invalid.  A pinhole pixel outside the
+// image was given depth 0, which is invalid; its ray is computed and unused.
+// Pinhole rays: d = (fma(M0, rx, c0), fma(M3, rx, c1), fma(M6, rx, c2)) with
+// the row's c = fma(M[3k+1], ry, M[3k+2]) staged once per tile row.
 template <bool PINHOLE_ONLY>
 __device__ __forceinline__ bool pixel_segment(const FrameDev& F, const MapDev& m,
                                               const float* s_ray, int i, int j, int lane, int ty,
                                               float d, float& dx, float& dy, float& dz, float& s0,
                                               float& s1) {
-  if (i >= F.width || j >= F.height) return false;
   bool valid;
   if (PINHOLE_ONLY || F.kind == kSensorPinhole) {
     valid = d > 0.0f && d <= FLT_MAX;
-    const float rx = s_ray[lane], ry = s_ray[kTileW + ty];
-    dx = __fmaf_rn(F.M[0], rx, __fmaf_rn(F.M[1], ry, F.M[2]));
-    dy = __fmaf_rn(F.M[3], rx, __fmaf_rn(F.M[4], ry, F.M[5]));
-    dz = __fmaf_rn(F.M[6], rx, __fmaf_rn(F.M[7], ry, F.M[8]));
+    const float rx = s_ray[lane];
+    const float4 c = reinterpret_cast<const float4*>(s_ray + kTileW)[ty];
+    dx = __fmaf_rn(F.M[0], rx, c.x);
+    dy = __fmaf_rn(F.M[3], rx, c.y);
+    dz = __fmaf_rn(F.M[6], rx, c.z);
   } else {
+    if (i >= F.width || j >= F.height) return false;
     valid = d >= F.min_range && d <= F.max_range;
     const float2 az = __ldg(reinterpret_cast<const float2*>(F.tab) + i);
     const float2 el = __ldg(reinterpret_cast<const float2*>(F.tab) + F.width + j);
@@ -246,7 +250,9 @@ struct AllocSmem {
   uint32_t set[kSetSize];   // CTA-local set of relative block keys
   uint32_t keys[kSetSize];  // the set's keys, compacted
   uint32_t nkeys;
-  float ray[kTileW + TH];   // pinhole: (i - cu) / fu per column, (j - cv) / fv per row
+  // pinhole: rx = (i - cu) / fu per column, then per row the three
+  // fma(M[3k+1], ry, M[3k+2]) with ry = (j - cv) / fv (and one pad word)
+  __align__(16) float ray[kTileW + 4 * TH];
 };
 
 // Allocation tile `cta` of the batch (tiles are numbered frame by frame,
@@ -291,8 +297,12 @@ __device__ __forceinline__ void alloc_tile(const BatchParams<NF, NM>& p, int cta
   if (PINHOLE_ONLY || F.kind == kSensorPinhole) {
     if (threadIdx.x < kTileW)
       s_ray[threadIdx.x] = __fdiv_rn(__fsub_rn((float)(x0 + (int)threadIdx.x), F.cu), F.fu);
-    else if (threadIdx.x < kTileW + TH)
-      s_ray[threadIdx.x] = __fdiv_rn(__fsub_rn((float)(y0 + (int)threadIdx.x - kTileW), F.cv), F.fv);
+    else if (threadIdx.x < kTileW + TH) {
+      const float ry = __fdiv_rn(__fsub_rn((float)(y0 + (int)threadIdx.x - kTileW), F.cv), F.fv);
+      reinterpret_cast<float4*>(s_ray + kTileW)[threadIdx.x - kTileW] =
+          make_float4(__fmaf_rn(F.M[1], ry, F.M[2]), __fmaf_rn(F.M[4], ry, F.M[5]),
+                      __fmaf_rn(F.M[7], ry, F.M[8]), 0.0f);
+    }
   }
   __syncthreads();
 
@@ -308,7 +318,7 @@ __device__ __forceinline__ void alloc_tile(const BatchParams<NF, NM>& p, int cta
       const float px = __fmaf_rn(s0, dx, F.o[0]), py = __fmaf_rn(s0, dy, F.o[1]),
                   pz = __fmaf_rn(s0, dz, F.o[2]);
       if (fabsf(px) < kRelStart && fabsf(py) < kRelStart && fabsf(pz) < kRelStart) {
-        wk.start<FAST>(px, py, pz, F.o[0], F.o[1], F.o[2], dx, dy, dz, s1, 0, 0, 0, 0u);
+        wk.start<FAST>(px, py, pz, dx, dy, dz, s1, 0, 0, 0, 0u);
         live = true;
       } else if (fabsf(px) < 262144.0f && fabsf(py) < 262144.0f && fabsf(pz) < 262144.0f) {
         // far from the sensor's block (long range or small voxels): count
@@ -316,7 +326,7 @@ __device__ __forceinline__ void alloc_tile(const BatchParams<NF, NM>& p, int cta
         b0x = (int)floorf(px);
         b0y = (int)floorf(py);
         b0z = (int)floorf(pz);
-        wk.start<FAST>(px, py, pz, F.o[0], F.o[1], F.o[2], dx, dy, dz, s1, b0x, b0y, b0z, kFarFlag);
+        wk.start<FAST>(px, py, pz, dx, dy, dz, s1, b0x, b0y, b0z, kFarFlag);
         live = true;
       }
     }
