@@ -57,6 +57,18 @@ __device__ __forceinline__ float rcp_dec(float x) {
   return __fmaf_rn(y, e, y);
 }
 
+// rcp_dec of a pair: the two refinement steps on the paired FP32
+// operations (per component the same round-to-nearest result).
+template <bool FAST>
+__device__ __forceinline__ float2 rcp_dec2(float a, float b) {
+  if (!FAST) return make_float2(__frcp_rn(a), __frcp_rn(b));
+  float2 y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y.x) : "f"(a));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y.y) : "f"(b));
+  const float2 e = __ffma2_rn(make_float2(-a, -b), y, make_float2(1.0f, 1.0f));
+  return __ffma2_rn(y, e, y);
+}
+
 // ------------------------------------------------------------------ hash
 
 __device__ __forceinline__ int hash_insert(const MapDev& m, unsigned long long key, bool& inserted) {
@@ -670,7 +682,7 @@ __device__ __forceinline__ void fuse_pinhole(const P& p, const FrameProj* s_fp, 
     const float2 half = make_float2(0.5f, 0.5f);
 #pragma unroll
     for (int i = 0; i < 4; i += 2) {
-      const float2 iz = make_float2(rcp_dec<FAST>(z[q][i]), rcp_dec<FAST>(z[q][i + 1]));
+      const float2 iz = rcp_dec2<FAST>(z[q][i], z[q][i + 1]);
       const float2 u = __fadd2_rn(__ffma2_rn(__fmul2_rn(make_float2(px[i], px[i + 1]), iz), fu2, cu2), half);
       const float2 v = __fadd2_rn(__ffma2_rn(__fmul2_rn(make_float2(py[i], py[i + 1]), iz), fv2, cv2), half);
       uu[i] = u.x; uu[i + 1] = u.y;
@@ -705,7 +717,8 @@ __device__ __forceinline__ void fuse_pinhole(const P& p, const FrameProj* s_fp, 
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const float dp = __fsub_rn(d[q][i], z[q][i]);
-      if (d[q][i] > 0.0f && d[q][i] <= FLT_MAX && !(dp < -m.tau)) {
+      // a valid depth, 0 < d <= FLT_MAX: one unsigned comparison of its bits
+      if ((__float_as_uint(d[q][i]) - 1u) < 0x7F7FFFFFu && !(dp < -m.tau)) {
         if (STORAGE == kStorageColor) {
           if (dp > m.tau) continue;
           apply_color(m, D[i], G[i], B[i], W[i], c[q][i]);
