@@ -655,13 +655,16 @@ __device__ __forceinline__ void row_points_staged(const float4& r0, const float4
   }
 }
 
+// PAIRED_RCP: the projection reciprocals refined on the paired operations
+// (pinhole-only kernels; in the kernels with the LiDAR path it raised the
+// register count from 72 to 79, one resident CTA per SM fewer).
 // NQ consecutive pinhole frames of the batch: phase 1 projects every voxel
 // into every frame (Eq. 2, nearest pixel) and issues all depth loads (and
 // colour loads for a colour layer), phase 2 applies the updates in frame
 // order.  An out-of-image projection reads no pixel and yields d = 0, which
 // is invalid like a missing depth.  A colour layer updates only voxels within
 // tau of the surface on both sides.
-template <int NQ, int STORAGE, bool WEIGHTED, bool FAST, class P>
+template <int NQ, int STORAGE, bool WEIGHTED, bool FAST, bool PAIRED_RCP, class P>
 __device__ __forceinline__ void fuse_pinhole(const P& p, const FrameProj* s_fp, const int (&fq)[4],
                                              const MapDev& m, const VoxelRow& r, float* D, float* W,
                                              float* G, float* B, unsigned long long& upd) {
@@ -682,7 +685,8 @@ __device__ __forceinline__ void fuse_pinhole(const P& p, const FrameProj* s_fp, 
     const float2 half = make_float2(0.5f, 0.5f);
 #pragma unroll
     for (int i = 0; i < 4; i += 2) {
-      const float2 iz = rcp_dec2<FAST>(z[q][i], z[q][i + 1]);
+      const float2 iz = PAIRED_RCP ? rcp_dec2<FAST>(z[q][i], z[q][i + 1])
+                                   : make_float2(rcp_dec<FAST>(z[q][i]), rcp_dec<FAST>(z[q][i + 1]));
       const float2 u = __fadd2_rn(__ffma2_rn(__fmul2_rn(make_float2(px[i], px[i + 1]), iz), fu2, cu2), half);
       const float2 v = __fadd2_rn(__ffma2_rn(__fmul2_rn(make_float2(py[i], py[i + 1]), iz), fv2, cv2), half);
       uu[i] = u.x; uu[i + 1] = u.y;
@@ -913,8 +917,10 @@ __device__ __forceinline__ void integrate_entries(const BatchParams<NF, NM>& p, 
           }
         }
         fq[2] = fq[3] = -1;
-        if (nq == 2) fuse_pinhole<2, STORAGE, WEIGHTED, FAST>(p, sm.fp, fq, m, vr, D, W, G4, B, my_upd);
-        else if (nq == 1) fuse_pinhole<1, STORAGE, WEIGHTED, FAST>(p, sm.fp, fq, m, vr, D, W, G4, B, my_upd);
+        if (nq == 2)
+          fuse_pinhole<2, STORAGE, WEIGHTED, FAST, PINHOLE_ONLY>(p, sm.fp, fq, m, vr, D, W, G4, B, my_upd);
+        else if (nq == 1)
+          fuse_pinhole<1, STORAGE, WEIGHTED, FAST, PINHOLE_ONLY>(p, sm.fp, fq, m, vr, D, W, G4, B, my_upd);
         else if (!PINHOLE_ONLY) {
           const int f = __ffs(bits) - 1;  // a LiDAR frame
           bits &= bits - 1u;
