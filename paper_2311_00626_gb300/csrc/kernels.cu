@@ -159,7 +159,10 @@ struct Walk32 {
   // The crossing parameters are recomputed from the boundaries at every
   // step, not carried: they are dead while the cell's key is recorded (at 32
   // registers a thread, carrying them spilled 88 bytes; 94.6 against 97.7 us
-  // per 32-frame launch).
+  // per 32-frame launch).  CAP: stop after kMaxCells cells; without it the
+  // host has proved that every segment of the batch ends sooner (the cell
+  // count then needs no register and no test).
+  template <bool CAP>
   __device__ __forceinline__ bool next(float ox, float oy, float oz) {
     const float tx = __fmul_rn(__fsub_rn(bx, ox), ix);
     const float ty = __fmul_rn(__fsub_rn(by, oy), iy);
@@ -168,7 +171,7 @@ struct Walk32 {
     const float t01 = fminf(tx, ty);
     const bool sz_ = tz < t01;
     const float t = fminf(t01, tz);
-    if (!(t <= s1) || n == kMaxCells) return false;
+    if (!(t <= s1) || (CAP && n == kMaxCells)) return false;
     const bool sx_ = !sz_ && !sy_, syy = !sz_ && sy_;
     const uint32_t dk = sz_ ? kz : (sy_ ? ky : kx);
     key += dk;
@@ -179,7 +182,7 @@ struct Walk32 {
     if (sx_) bx = __fadd_rn(bx, f);
     if (syy) by = __fadd_rn(by, f);
     if (sz_) bz = __fadd_rn(bz, f);
-    ++n;
+    if (CAP) ++n;
     return true;
   }
 };
@@ -192,21 +195,29 @@ __device__ __forceinline__ unsigned long long rel_to_key(uint32_t r, const int* 
 }
 constexpr uint32_t kFarFlag = 1u << 30;  // key counted from the segment's own start cell
 
-// CTA-local set of relative block keys (open addressing in shared memory).
-// Returns false when the key could not be placed within kSetProbes slots;
+// CTA-local set of relative block keys (open addressing in shared memory):
+// `set` holds kSetSize slots, `keys` receives each key when it first enters
+// the set (appended at *nkeys), so the tile's distinct blocks need no scan of
+// the slots afterwards.  Returns false when the key could not be placed
+// within kSetProbes slots, or is a far segment's key (bit 30: counted from
+// the segment's own start cell, never in the set; it cannot match a slot,
+// which holds a near key or kEmptyRel, so it always reaches the slow path);
 // the caller then claims it globally itself.  The probing loop is inlined:
 // at the allocator's 32 registers a call's saves and restores cost more
 // than the larger code (measured 5 % slower as a call).
-__device__ __forceinline__ bool set_insert_slow(uint32_t* set, uint32_t key, uint32_t h);
+__device__ __forceinline__ bool set_insert_slow(uint32_t* set, uint32_t* keys, uint32_t* nkeys,
+                                                uint32_t key, uint32_t h);
 
-__device__ __forceinline__ bool set_insert(uint32_t* set, uint32_t key) {
+__device__ __forceinline__ bool set_insert(uint32_t* set, uint32_t* keys, uint32_t* nkeys, uint32_t key) {
   const uint32_t h = (key * 0x9E3779B1u) >> (32 - kSetBits);
   // common case: the key is already at its home slot
   if (((volatile uint32_t*)set)[h] == key) return true;
-  return set_insert_slow(set, key, h);
+  return set_insert_slow(set, keys, nkeys, key, h);
 }
 
-__device__ __forceinline__ bool set_insert_slow(uint32_t* set, uint32_t key, uint32_t h) {
+__device__ __forceinline__ bool set_insert_slow(uint32_t* set, uint32_t* keys, uint32_t* nkeys,
+                                                uint32_t key, uint32_t h) {
+  if (key & kFarFlag) return false;
   volatile uint32_t* vs = set;
 #pragma unroll 1
   for (int probe = 0; probe < kSetProbes; ++probe) {
@@ -214,7 +225,11 @@ __device__ __forceinline__ bool set_insert_slow(uint32_t* set, uint32_t key, uin
     if (cur == key) return true;
     if (cur == kEmptyRel) {
       const uint32_t old = atomicCAS(set + h, kEmptyRel, key);
-      if (old == kEmptyRel || old == key) return true;
+      if (old == kEmptyRel) {
+        keys[atomicAdd(nkeys, 1u)] = key;  // at most kSetSize distinct keys
+        return true;
+      }
+      if (old == key) return true;
     }
     h = (h + 1) & (kSetSize - 1);
   }
@@ -260,7 +275,7 @@ __device__ __forceinline__ bool pixel_segment(const FrameDev& F, const MapDev& m
 template <int TH>
 struct AllocSmem {
   uint32_t set[kSetSize];   // CTA-local set of relative block keys
-  uint32_t keys[kSetSize];  // the set's keys, compacted
+  uint32_t keys[kSetSize];  // the set's keys, in order of first insertion
   uint32_t nkeys;
   // pinhole: rx = (i - cu) / fu per column, then per row the three
   // fma(M[3k+1], ry, M[3k+2]) with ry = (j - cv) / fv (and one pad word)
@@ -271,7 +286,7 @@ struct AllocSmem {
 // FrameDev::blk_begin being a frame's first), run by all kAllocThreads
 // threads of a CTA.  With p.overlap the stream's next kernel may be
 // scheduled once the walks are done.
-template <int NF, int NM, int TH, bool PINHOLE_ONLY, bool STATS, bool FAST>
+template <int NF, int NM, int TH, bool PINHOLE_ONLY, bool STATS, bool FAST, bool CAP>
 __device__ __forceinline__ void alloc_tile(const BatchParams<NF, NM>& p, int cta, AllocSmem<TH>& sm) {
   constexpr int kRows = TH * kTileW / kAllocThreads;  // pixel rows per thread
   uint32_t segs = 0, cells = 0;                        // walk statistics
@@ -346,22 +361,19 @@ __device__ __forceinline__ void alloc_tile(const BatchParams<NF, NM>& p, int cta
     while (__any_sync(0xffffffffu, live)) {
       if (live) {
         ++cells;
-        if (wk.key & kFarFlag)
-          claim_block(m, rel_to_key(wk.key & ~kFarFlag, F.a, b0x, b0y, b0z), F.bit);
-        else if (!set_insert(s_set, wk.key))
-          claim_block(m, rel_to_key(wk.key, F.a), F.bit);
-        live = wk.next(F.o[0], F.o[1], F.o[2]);
+        if (!set_insert(s_set, s_keys, &sm.nkeys, wk.key)) {
+          if (wk.key & kFarFlag)
+            claim_block(m, rel_to_key(wk.key & ~kFarFlag, F.a, b0x, b0y, b0z), F.bit);
+          else
+            claim_block(m, rel_to_key(wk.key, F.a), F.bit);
+        }
+        live = wk.template next<CAP>(F.o[0], F.o[1], F.o[2]);
       }
     }
   }
   if (p.overlap) allow_next_grid();
   __syncthreads();
-  // compact the tile's distinct blocks, then claim them one per thread
-  for (int i = threadIdx.x; i < kSetSize; i += kAllocThreads) {
-    const uint32_t key = s_set[i];
-    if (key != kEmptyRel) s_keys[atomicAdd(&sm.nkeys, 1u)] = key;
-  }
-  __syncthreads();
+  // the tile's distinct blocks, claimed one per thread
   const uint32_t nk = sm.nkeys;
   for (uint32_t i = threadIdx.x; i < nk; i += kAllocThreads) claim_block(m, rel_to_key(s_keys[i], F.a), F.bit);
   if (STATS) {
@@ -383,13 +395,14 @@ __device__ __forceinline__ void alloc_tile(const BatchParams<NF, NM>& p, int cta
 // their own start cell and claim their blocks directly.  PINHOLE_ONLY: every
 // frame of the batch is a pinhole camera (the LiDAR code is left out);
 // STATS: count band segments and walked cells (a diagnostic, 5 % slower);
-// FAST: reciprocals by rcp_dec<true> (the host checked their range).
-template <int NF, int NM, int TH, bool PINHOLE_ONLY, bool STATS, bool FAST>
+// FAST: reciprocals by rcp_dec<true> (the host checked their range); CAP:
+// walks stop after kMaxCells cells (without it the host proved them shorter).
+template <int NF, int NM, int TH, bool PINHOLE_ONLY, bool STATS, bool FAST, bool CAP>
 __global__ void __launch_bounds__(kAllocThreads, 7)
     band_alloc_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
   if (p.overlap) wait_prev_grid();
   __shared__ AllocSmem<TH> sm;
-  alloc_tile<NF, NM, TH, PINHOLE_ONLY, STATS, FAST>(p, (int)blockIdx.x, sm);
+  alloc_tile<NF, NM, TH, PINHOLE_ONLY, STATS, FAST, CAP>(p, (int)blockIdx.x, sm);
 }
 
 // ------------------------------------------------ per-voxel projection
@@ -1037,7 +1050,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4)
     fused_kernel(const __grid_constant__ BatchParams<NF, NM> p) {
   __shared__ FusedSmem<NF, NM, TH> sm;
   for (int cta = blockIdx.x; cta < p.alloc_ctas; cta += gridDim.x)
-    alloc_tile<NF, NM, TH, PINHOLE_ONLY, false, FAST>(p, cta, sm.a);
+    alloc_tile<NF, NM, TH, PINHOLE_ONLY, false, FAST, true>(p, cta, sm.a);
   if (!grid_wait(p.maps[0].ctl + 3, gridDim.x + (unsigned)p.wait_extra, p.maps[0].counters + kCntStatus))
     return;  // timed out: integration skipped, the map reports TSDF_ERR_TIMEOUT
   integrate_entries<NF, NM, 2, true, STORAGE, PINHOLE_ONLY, false, FAST>(p, sm.i);
@@ -1154,6 +1167,14 @@ bool pinhole_only(const BatchParams<NF, NM>& p) {
   return true;
 }
 
+// Every frame's band segments meet fewer than kMaxCells blocks (host check).
+template <int NF, int NM>
+bool short_walks(const BatchParams<NF, NM>& p) {
+  for (int f = 0; f < p.n_frames; ++f)
+    if (!p.fr[f].short_walks) return false;
+  return true;
+}
+
 // Launch kernel k; with p.overlap as a programmatic dependent launch.
 template <class P>
 cudaError_t launch_k(void (*k)(P), dim3 g, dim3 b, cudaStream_t s, const P& p) {
@@ -1179,21 +1200,27 @@ cudaError_t launch_band_alloc(const BatchParams<NF, NM>& p, int n_ctas, int tile
   const dim3 g(n_ctas), b(kAllocThreads);
   if (st) {  // diagnostics: one generic variant per tile height
     if (tile_h == kTileHBig)
-      return launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, true, false>, g, b, s, p);
+      return launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, true, false, true>, g, b, s, p);
     else
-      return launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, true, false>, g, b, s, p);
+      return launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, true, false, true>, g, b, s, p);
+  }
+  if (!short_walks(p)) {  // segments that may reach the cap: one generic variant per tile height
+    if (tile_h == kTileHBig)
+      return launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, false, false, true>, g, b, s, p);
+    else
+      return launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, false, false, true>, g, b, s, p);
   }
   const bool fast = p.fast_rcp != 0;
   if (tile_h == kTileHBig) {
-    if (ph) return fast ? launch_k(band_alloc_kernel<NF, NM, kTileHBig, true, false, true>, g, b, s, p)
-                        : launch_k(band_alloc_kernel<NF, NM, kTileHBig, true, false, false>, g, b, s, p);
-    return fast ? launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, false, true>, g, b, s, p)
-                : launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, false, false>, g, b, s, p);
+    if (ph) return fast ? launch_k(band_alloc_kernel<NF, NM, kTileHBig, true, false, true, false>, g, b, s, p)
+                        : launch_k(band_alloc_kernel<NF, NM, kTileHBig, true, false, false, false>, g, b, s, p);
+    return fast ? launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, false, true, false>, g, b, s, p)
+                : launch_k(band_alloc_kernel<NF, NM, kTileHBig, false, false, false, false>, g, b, s, p);
   }
-  if (ph) return fast ? launch_k(band_alloc_kernel<NF, NM, kTileHSmall, true, false, true>, g, b, s, p)
-                      : launch_k(band_alloc_kernel<NF, NM, kTileHSmall, true, false, false>, g, b, s, p);
-  return fast ? launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, false, true>, g, b, s, p)
-              : launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, false, false>, g, b, s, p);
+  if (ph) return fast ? launch_k(band_alloc_kernel<NF, NM, kTileHSmall, true, false, true, false>, g, b, s, p)
+                      : launch_k(band_alloc_kernel<NF, NM, kTileHSmall, true, false, false, false>, g, b, s, p);
+  return fast ? launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, false, true, false>, g, b, s, p)
+              : launch_k(band_alloc_kernel<NF, NM, kTileHSmall, false, false, false, false>, g, b, s, p);
 }
 
 template <int NF, int NM>

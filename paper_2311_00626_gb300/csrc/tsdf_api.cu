@@ -220,6 +220,29 @@ bool fast_rcp_ok(const FrameDev& F, double v, int lidar_lsb) {
   return L >= -126 && 3.0 * max_m * (1.0 + 1e-6) < kTwo126;
 }
 
+// Whether every band segment of frame F provably meets fewer than
+// kMaxCells blocks, so the allocation kernel may walk without the cap.  A
+// segment spans s1 - s0 <= 2 tau of depth or range (plus at most d 2^-23 from
+// rounding its two ends, under 0.06 blocks at the distances walked) along a
+// direction of length |r| / B in blocks per unit, r = (rx, ry, 1) for a
+// pinhole pixel (largest at an image corner) and a unit beam for a LiDAR:
+// L <= (2 tau / B) |r| = (trunc / 4) |r| blocks.  Along each axis the FP32
+// traversal crosses at most |dp_k| + 2 boundaries (the three roundings of a
+// crossing parameter and the rounded start point move a boundary test by
+// less than one cell), so a segment meets at most 7 + sqrt(3) (L + 0.06)
+// cells; L <= 8 keeps that under 22.
+bool short_walks_ok(const FrameDev& F, int32_t trunc) {
+  double r2 = 1.0;
+  if (F.kind == TSDF_SENSOR_PINHOLE) {
+    const double ax = std::max(std::fabs(-(double)F.cu / (double)F.fu),
+                               std::fabs(((double)F.width - 1.0 - (double)F.cu) / (double)F.fu));
+    const double ay = std::max(std::fabs(-(double)F.cv / (double)F.fv),
+                               std::fabs(((double)F.height - 1.0 - (double)F.cv) / (double)F.fv));
+    r2 += ax * ax + ay * ay;
+  }
+  return 0.25 * (double)trunc * std::sqrt(r2) * (1.0 + 1e-3) <= 8.0;
+}
+
 // Beam-centre direction tables of a LiDAR (Eq. 3 inverted at the cell
 // centres), computed in FP64 and rounded once; uploaded on first use.
 tsdf_status lidar_table(tsdf_map* m, const tsdf_lidar* c, const float** out, int* lsb) {
@@ -306,6 +329,7 @@ tsdf_status fill_frame(tsdf_map* m, int map_index, int kind, const tsdf_pinhole*
   }
   if (!prepare_pose(m->Bd, T, F)) return TSDF_ERR_ARG;
   F.fast_rcp = fast_rcp_ok(F, m->vd, lidar_lsb) ? 1 : 0;
+  F.short_walks = short_walks_ok(F, m->trunc) ? 1 : 0;
   return TSDF_OK;
 }
 
@@ -1487,6 +1511,7 @@ tsdf_status integrate_depth_static(const tsdf_map_buffers* buf, float voxel_size
   F.bit = 0;
   if (!prepare_pose(8.0 * (double)voxel_size, T_world_cam, F)) return TSDF_ERR_ARG;
   p.fast_rcp = fast_rcp_ok(F, (double)voxel_size, INT_MAX) ? 1 : 0;
+  F.short_walks = short_walks_ok(F, truncation_voxels) ? 1 : 0;
 
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||

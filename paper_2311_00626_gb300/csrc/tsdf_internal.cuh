@@ -149,6 +149,7 @@ struct FrameDev {
   int32_t blk_begin;     // first allocation CTA of this frame
   int32_t bit;           // bit of this frame in the slot masks = its index in the batch
   int32_t fast_rcp;      // host check: this frame's inverted decision values are in [2^-126, 2^126]
+  int32_t short_walks;   // host check: this frame's band segments meet fewer than kMaxCells blocks
 };
 
 template <int NF, int NM>
