@@ -313,6 +313,43 @@ def test_dda_cap_keeps_the_first_cells():
     assert checked >= 1000 and capped >= 900, (checked, capped)
 
 
+def test_short_segments_stay_below_the_cap():
+    """The allocation kernels drop the 32-cell cap for batches whose band
+    segments span at most 8 blocks ((trunc / 4) |r| <= 8 on the host, r the
+    widest pixel ray or a unit beam), on the bound that a segment of L blocks
+    meets at most 7 + sqrt(3) (L + 0.06) cells under FP32 rounding (at most
+    |dp_k| + 2 boundaries per axis).  Checked on the oracle's traversal with
+    segments of exactly 8 blocks: random directions, the main diagonal (most
+    crossings per length), starts a few ulp from block faces, and starts far
+    from the anchor (coarse FP32 spacing)."""
+    rng = np.random.default_rng(13)
+    L = 8.0
+    bound = 7 + np.sqrt(3.0) * (L + 0.06)
+    worst = 0
+    for it in range(6000):
+        o = rng.uniform(0, 1, 3).astype(np.float32)
+        kind = it % 3
+        if kind == 0:
+            d = rng.normal(size=3)
+        else:  # close to a main diagonal
+            d = rng.choice([-1.0, 1.0], 3) + rng.normal(scale=1e-3, size=3)
+        d = (d / np.linalg.norm(d) * rng.uniform(0.2, 12.0)).astype(np.float32)
+        nd = float(np.linalg.norm(d.astype(np.float64)))
+        far = rng.uniform() < 0.3
+        s0 = np.float32(rng.uniform(0, (200000.0 if far else 400.0) / nd))
+        if kind == 2:  # start a few ulp off a block face on one axis
+            k = int(rng.integers(3))
+            p = np.float64(o[k]) + np.float64(s0) * np.float64(d[k])
+            target = np.round(p) + rng.choice([-1, 1]) * rng.integers(0, 4) * np.spacing(np.float32(p))
+            if d[k] != 0.0:
+                s0 = np.float32(max(0.0, (target - np.float64(o[k])) / np.float64(d[k])))
+        s1 = np.float32(np.float64(s0) + L / nd)
+        n = len(oracle.dda(o, d, float(s0), float(s1)))
+        worst = max(worst, n)
+        assert n <= bound, (o, d, s0, s1, n)
+    assert worst < 32 and worst >= 14, worst
+
+
 # ------------------------------------------------------------------ LiDAR
 
 
